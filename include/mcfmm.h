@@ -1,0 +1,132 @@
+/*
+ * mcfmm: GB300 (sm_103a) library for the multilevel local-expansion
+ * Metropolis-Hastings electrostatics method of Saunders, Grant & Mueller,
+ * "A new algorithm for electrostatic interactions in Monte Carlo simulations
+ * of charged particles" (arXiv 2006.16622).
+ *
+ * C ABI: plain pointers and sizes only.  Every call returns MC_OK (0) or a
+ * negative MC_ERR_* status; mc_strerror() names it.  The library owns all
+ * device memory of a context; inputs are copied, the caller keeps ownership
+ * of its arrays.  Calls on one context are not thread safe.
+ *
+ * Conventions
+ *   - the box is the cube [0, a)^3; positions are (n, 3) row-major doubles;
+ *   - p is the expansion order (largest n of Eq. 2), 0 <= p <= 15; an
+ *     expansion has (p+1)^2 real numbers in the "real layout": for each n,
+ *     Re X_n^0 then (Re X_n^m, Im X_n^m) for m = 1..n (X_n^-m = conj X_n^m);
+ *   - level l (1 = whole box) has 2^(l-1) cells per axis; cell (i, j, k) of a
+ *     level has linear index (i * n_l + j) * n_l + k;
+ *   - coefficients use the normalisation Y_n^m = sqrt((n-|m|)!/(n+|m|)!)
+ *     P_n^|m|(cos t) e^{i m phi} (no Condon-Shortley phase);
+ *   - energies are in units of q^2 / length (Gaussian units, unit charges).
+ */
+#ifndef MCFMM_H
+#define MCFMM_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MC_OK 0
+#define MC_ERR_ARG (-1)        /* invalid argument (null pointer, size, index) */
+#define MC_ERR_NONNEUTRAL (-2) /* periodic boundaries need sum q = 0 */
+#define MC_ERR_LEVELS (-4)     /* levels outside 2..8 */
+#define MC_ERR_OUTSIDE (-5)    /* a position outside [0, a)^3 */
+#define MC_ERR_CUDA (-6)       /* a CUDA runtime call failed */
+#define MC_ERR_TIMEOUT (-7)    /* a device-side wait gave up (bounded spin) */
+#define MC_ERR_CAPACITY (-8)   /* a finest cell overflowed its slot capacity */
+#define MC_ERR_ORDER (-9)      /* expansion order p outside 0..15 */
+#define MC_ERR_STATE (-10)     /* call out of order (e.g. propose before setup) */
+#define MC_ERR_NOMEM (-11)     /* device allocation failed */
+
+#define MC_BC_PBC 0   /* periodic cube (paper Sec. 3.3) */
+#define MC_BC_FREE 1  /* free space (paper Sec. 3.3, first paragraph) */
+#define MC_TINFOIL 0  /* conducting surroundings: dipole term removed */
+#define MC_VACUUM 1   /* cubic-shell (vacuum) summation of the images */
+#define MC_FP64 0     /* every step in FP64 */
+#define MC_FP32_EVAL 1 /* harmonics and near field in FP32; FP64 accumulators,
+                          energy and periodic lattice term */
+#define MC_SETUP_P2L 0 /* Alg. L.3 as a per-target gather */
+
+typedef struct mc_ctx mc_ctx;
+
+typedef struct {
+  int64_t steps;      /* proposals made by the last mc_run */
+  int64_t accepted;   /* accepted proposals */
+  int64_t borderline; /* decisions within 1e-9 (relative) of the threshold */
+  int64_t resetups;   /* full re-setups done by the last mc_run */
+  double energy;      /* running total energy after the run */
+  double max_drift;   /* max |running - fresh| energy seen at a re-setup */
+} mc_stats;
+
+/* Create a context (paper Sec. 4, the MCFMM_LM constructor).
+ *   n            number of charges (>= 1)
+ *   pos, q       host arrays, (n, 3) positions in [0, box)^3 and n charges
+ *   box          cube side a > 0
+ *   levels       octree levels L, 2..8 (finest level has 8^(L-1) cells)
+ *   p            expansion order 0..15
+ *   bc           MC_BC_PBC or MC_BC_FREE; PBC needs sum q = 0 (|sum| < 1e-9)
+ *   dipole_bc    MC_TINFOIL or MC_VACUUM (ignored for MC_BC_FREE)
+ *   precision    MC_FP64 or MC_FP32_EVAL
+ *   cuda_stream  cudaStream_t the context launches on, NULL = legacy stream
+ * Allocates device memory; the expansions are undefined until mc_setup. */
+int mc_init(mc_ctx **out, int64_t n, const double *pos, const double *q, double box,
+            int levels, int p, int bc, int dipole_bc, int precision, void *cuda_stream);
+
+/* Alg. L.3 (initialise local expansions), the box multipole K/E of
+ * Sec. 3.3 (ii), the lattice local expansion H = R(K) and the total energy.
+ * mode: MC_SETUP_P2L.  Synchronous. */
+int mc_setup(mc_ctx *ctx, int mode);
+
+/* Alg. L.1 with Alg. 1 and the periodic terms of Sec. 3.3: the energy change
+ * of moving charge j (0 <= j < n) to r_new in [0, a)^3.  Writes +inf when
+ * r_new coincides with another charge.  Synchronous. */
+int mc_propose(mc_ctx *ctx, int64_t j, const double r_new[3], double *dE_out);
+
+/* Alg. L.2 with the K/E update of Sec. 3.3 (iii): accept the move of j to
+ * r_new.  dE_or_null: the energy change to add to the running energy; NULL
+ * recomputes it with Alg. L.1 first (as the paper's accept() does). */
+int mc_accept(mc_ctx *ctx, int64_t j, const double r_new[3], const double *dE_or_null);
+
+/* Metropolis-Hastings chain of n_steps proposals in one persistent launch.
+ * Proposal t (global step counter s, which continues across calls) draws
+ * j, a displacement uniform in [-h, h]^3 and u uniform in [0, 1) from
+ * Philox4x32-10 keyed by seed; the move is accepted iff dE <= 0 or
+ * log(u) < -beta dE.  resetup_every_accepts > 0 re-runs mc_setup after that
+ * many accepts and records the running-minus-fresh energy drift.
+ * stats/log arrays may be NULL; when all are NULL and resetup is 0 the call
+ * only enqueues the launch on the context stream and returns.  The log
+ * arrays are host arrays of n_steps entries (moved charge, dE, accepted). */
+int mc_run(mc_ctx *ctx, int64_t n_steps, uint64_t seed, double beta, double half_width,
+           int64_t resetup_every_accepts, mc_stats *stats, int64_t *log_j, double *log_dE,
+           uint8_t *log_acc);
+
+/* Running total energy (setup energy plus accepted changes). */
+int mc_energy(mc_ctx *ctx, double *e_out);
+/* Total energy recomputed from the current expansions and positions. */
+int mc_energy_fresh(mc_ctx *ctx, double *e_out);
+/* Current positions (n, 3) into a host array. */
+int mc_get_positions(mc_ctx *ctx, double *pos_out);
+/* Local coefficients L^Delta of level l (2..L), all cells, real layout,
+ * paper normalisation; host array of 8^(l-1) * (p+1)^2 doubles. */
+int mc_get_local(mc_ctx *ctx, int level, double *out);
+/* Box multipole K and lattice local expansion H = R(K), real layout, paper
+ * normalisation; host arrays of (p+1)^2 doubles (zeros for MC_BC_FREE). */
+int mc_get_far(mc_ctx *ctx, double *K_out, double *H_out);
+/* Lattice sums S_l^m = sum over integer v with max|v_i| >= 2 of
+ * Y_l^m(v/|v|)/|v|^(l+1), l <= lmax <= 30, as computed on the device;
+ * complex interleaved, index 2*(l*l + l + m). */
+int mc_lattice_sums(int lmax, double *out);
+/* Status of the last asynchronous launch (MC_OK, MC_ERR_TIMEOUT, ...). */
+int mc_status(mc_ctx *ctx);
+/* Wait-limit of the device-side grid barrier in nanoseconds (default 2e9);
+ * a wait that runs out sets MC_ERR_TIMEOUT and the launch returns. */
+int mc_set_wait_limit(mc_ctx *ctx, int64_t ns);
+void mc_destroy(mc_ctx *ctx);
+const char *mc_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,312 @@
+// Device-side data layout and building blocks of the GB300 multilevel
+// Monte Carlo electrostatics library (Saunders, Grant & Mueller,
+// arXiv 2006.16622).
+//
+// Representation.  Expansion coefficients are kept in a scaled real layout
+// that removes every normalisation constant from the hot loops:
+//   Lhat_n^m = L_n^m * s_nm,   s_nm = sqrt((n-m)! (n+m)!),   m >= 0,
+// so that (Eq. 2)   Psi(x) = sum_n [Lhat_n^0 Rt_n^0 + 2 Re sum_{m>0} Lhat_n^m Rt_n^m]
+// and (Alg. L.2)    Lhat_n^m += q conj(It_n^m(x_src - R_target))
+// with the scaled solid harmonics (P_n^m without Condon-Shortley phase)
+//   Rt_n^m(x) = r^n P_n^m(cos t) e^{i m phi} / (n+m)!
+//   It_n^m(x) = (n-m)! r^-(n+1) P_n^m(cos t) e^{i m phi}.
+// Real layout of one expansion: index n*n for m = 0, n*n + 2m - 1 (re) and
+// n*n + 2m (im) for m > 0; (p+1)^2 doubles.
+//
+// Both scaled harmonics obey the same two-term recurrences, run per column m
+// by one lane of a half-warp (lane = m, n advancing in lock step):
+//   diagonal (n <= m):  X_n = A_n (x + i y) X_{n-1}
+//   column   (n >  m):  X_n = A_nm z X_{n-1} - B_nm Q X_{n-2}
+// regular:   A = 1/(2n) | (2n-1)/((n+m)(n-m)),  B = 1/((n+m)(n-m)), Q = r^2
+// irregular: (x, y, z) -> (x, y, z)/r^2, A = 2n-1, B = (n+m-1)(n-m-1), Q = 1/r^2.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define MC_PMAX 15
+#define MC_MAXLEV 8
+#define MC_THREADS 256
+#define MC_WARPS (MC_THREADS / 32)
+#define MC_MAX_ITEMS 256
+#define MC_NF_ROWS 6    // far-field row blocks of 32 rows (covers C <= 192)
+#define MC_NF_COLS 8    // far-field column chunks
+
+// ---------------------------------------------------------------- state
+struct McSys {
+  int n, L, p, C, bc, dip, prec;
+  int nL, cap, ncellL, lmin, ncell_total;
+  double a, inv_wL, V;
+  int lev_off[MC_MAXLEV + 2];  // first cell of level l in Lhat
+  int lev_n[MC_MAXLEV + 2];    // cells per axis on level l
+  double lev_w[MC_MAXLEV + 2]; // cell width on level l
+  double4* ppos;     // [n]        (x, y, z, q) by particle id
+  double4* cpos;     // [ncellL*cap] slot positions (x, y, z, q)
+  float4* cpos32;    // [ncellL*cap] slot position relative to the cell centre, q
+  int* cpid;         // [ncellL*cap] particle id of a slot
+  int* ccount;       // [ncellL]
+  int* pslot;        // [n] slot of a particle
+  double* Lhat;      // [ncell_total * C] per-level local expansions
+  double* Khat;      // [C] box multipole (scaled, conj of regular harmonics)
+  double* Hhat;      // [C] lattice local expansion H = R(K) (scaled)
+  double* G;         // [C*C] real far-field operator: Hhat = G Khat
+  double* dipv;      // [3] dipole sum q r
+  double* energy;    // [1] running energy
+  double* partials;  // [2 * MC_MAX_ITEMS]
+  double* dK;        // [2 * C] change of Khat of the current proposal
+  double* gK;        // [2 * MC_NF_COLS * C] partial G dK of the current proposal
+  unsigned long long* bar;  // grid barrier counter
+  int* status;       // device status word (MC_OK or MC_ERR_*)
+  long long* stats;  // [4] steps, accepted, borderline, spare
+  double* result;    // [4] dE of a single proposal, ...
+};
+
+struct RunParams {
+  int mode;  // 0: chain with Philox proposals, 1: propose a given move, 2: accept a given move
+  long long step0, nsteps;
+  unsigned long long seed;
+  double beta, h;
+  long long jg;
+  double rx, ry, rz;
+  int has_dE;
+  double dEg;
+  long long stop_after_accepts;  // 0 = none
+  long long* log_j;
+  double* log_dE;
+  unsigned char* log_acc;
+  long long wait_ns;
+};
+
+// ------------------------------------------------------------ error codes
+#define MCD_OK 0
+#define MCD_ERR_TIMEOUT (-7)
+#define MCD_ERR_CAPACITY (-8)
+
+// ------------------------------------------------------------ Philox4x32-10
+// Salmon et al. (SC'11): two 32x32 multiplies per round, Weyl key bumps.
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; r++) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+    uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+    uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+  }
+}
+
+// Proposal of global step s: j = floor(A0 n / 2^32); delta_k = h (2u_k - 1),
+// u_k = (A_k + 1/2) 2^-32; acceptance uniform ((B0>>5) 2^26 + (B1>>6)) 2^-53.
+// Written with explicit round-to-nearest intrinsics so that no contraction
+// changes the bits of the displacement.
+__device__ __forceinline__ void mc_proposal(unsigned long long seed, unsigned long long s,
+                                            uint32_t chain, int n, double h, int* j,
+                                            double d[3], double* u) {
+  uint32_t A[4] = {(uint32_t)s, (uint32_t)(s >> 32), chain, 0u};
+  uint32_t B[4] = {(uint32_t)s, (uint32_t)(s >> 32), chain, 1u};
+  philox4x32_10(A, (uint32_t)seed, (uint32_t)(seed >> 32));
+  philox4x32_10(B, (uint32_t)seed, (uint32_t)(seed >> 32));
+  *j = (int)(((unsigned long long)A[0] * (unsigned long long)n) >> 32);
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    double uk = __dmul_rn(__dadd_rn((double)A[k + 1], 0.5), 2.3283064365386963e-10);
+    d[k] = __dmul_rn(h, __dsub_rn(__dmul_rn(2.0, uk), 1.0));
+  }
+  *u = __dmul_rn(__dadd_rn(__dmul_rn((double)(B[0] >> 5), 67108864.0), (double)(B[1] >> 6)),
+                 1.1102230246251565e-16);
+}
+
+// ---------------------------------------------------------- grid barrier
+// Monotone 64-bit arrival counter; thread 0 of every CTA arrives with a
+// release add and spins with acquire loads until all CTAs of this
+// generation arrived.  The spin is bounded by wall time (globaltimer): on
+// expiry the status word gets MCD_ERR_TIMEOUT and the caller leaves its loop.
+__device__ __forceinline__ unsigned long long mc_globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool grid_barrier(unsigned long long* ctr, unsigned long long target,
+                                             int* status, long long wait_ns) {
+  __syncthreads();
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(ctr) : "memory");
+    unsigned long long v;
+    unsigned long long t0 = mc_globaltimer();
+    int ok = 1;
+    unsigned spins = 0;
+    while (true) {
+      asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
+      if (v >= target) break;
+      if ((++spins & 255u) == 0u) {
+        if ((long long)(mc_globaltimer() - t0) > wait_ns) {
+          atomicExch(status, MCD_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        if (*((volatile int*)status) != MCD_OK) {
+          ok = 0;
+          break;
+        }
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ------------------------------------------------------ recurrence tables
+template <typename T>
+struct HarmTabs {
+  T rA[MC_PMAX + 1][16], rB[MC_PMAX + 1][16];  // regular
+  T iA[MC_PMAX + 1][16], iB[MC_PMAX + 1][16];  // irregular
+};
+
+template <typename T>
+__device__ void harm_tabs_init(HarmTabs<T>* t) {
+  for (int k = threadIdx.x; k < (MC_PMAX + 1) * 16; k += blockDim.x) {
+    int n = k / 16, m = k % 16;
+    double ra = 0, rb = 0, ia = 0, ib = 0;
+    if (n >= 1) {
+      if (n <= m) {
+        ra = 1.0 / (2.0 * n);
+        ia = 2.0 * n - 1.0;
+      } else {
+        double den = (double)(n + m) * (double)(n - m);
+        ra = (2.0 * n - 1.0) / den;
+        rb = 1.0 / den;
+        ia = 2.0 * n - 1.0;
+        ib = (double)(n + m - 1) * (double)(n - m - 1);
+      }
+    }
+    t->rA[n][m] = (T)ra;
+    t->rB[n][m] = (T)rb;
+    t->iA[n][m] = (T)ia;
+    t->iB[n][m] = (T)ib;
+  }
+}
+
+// Column m of the scaled harmonics for n = 0..p; use(n, re, im) is called
+// for every n (values are meaningful for n >= m).
+template <typename T, typename F>
+__device__ __forceinline__ void harm_columns(const T (*A)[16], const T (*B)[16], int p, int m,
+                                             T X, T Y, T Z, T Q, T start, F&& use) {
+  T p1r = start, p1i = T(0), p2r = T(0), p2i = T(0);
+  use(0, p1r, p1i);
+#pragma unroll
+  for (int n = 1; n <= MC_PMAX; n++) {
+    if (n <= p) {
+      const bool diag = n <= m;
+      const T ca = A[n][m], cb = B[n][m];
+      const T ar = (diag ? X : Z) * ca;
+      const T ai = diag ? Y * ca : T(0);
+      const T b = -Q * cb;
+      const T cr = ar * p1r - ai * p1i + b * p2r;
+      const T ci = ar * p1i + ai * p1r + b * p2i;
+      p2r = diag ? T(0) : p1r;
+      p2i = diag ? T(0) : p1i;
+      p1r = cr;
+      p1i = ci;
+      use(n, cr, ci);
+    }
+  }
+}
+
+// regular harmonics of displacement (x, y, z)
+template <typename T, typename F>
+__device__ __forceinline__ void regular_columns(const HarmTabs<T>* t, int p, int m, T x, T y, T z,
+                                                F&& use) {
+  T r2 = x * x + y * y + z * z;
+  harm_columns<T>(t->rA, t->rB, p, m, x, y, z, r2, T(1), use);
+}
+
+__device__ __forceinline__ double mc_rsqrt(double v) { return rsqrt(v); }
+__device__ __forceinline__ float mc_rsqrt(float v) { return rsqrtf(v); }
+
+// irregular harmonics of displacement (x, y, z) (source minus centre)
+template <typename T, typename F>
+__device__ __forceinline__ void irregular_columns(const HarmTabs<T>* t, int p, int m, T x, T y,
+                                                  T z, F&& use) {
+  T r2 = x * x + y * y + z * z;
+  T ir = mc_rsqrt(r2);
+  T ir2 = ir * ir;
+  harm_columns<T>(t->iA, t->iB, p, m, x * ir2, y * ir2, z * ir2, ir2, ir, use);
+}
+
+// index of (n, m) in the real layout (re part; im part is +1 for m > 0)
+__device__ __forceinline__ int rl_re(int n, int m) { return n * n + (m ? 2 * m - 1 : 0); }
+
+// ------------------------------------------------------------- geometry
+// Interaction-list offsets (Sec. 3.1) for the 8 parity classes of a cell:
+// children of the parent's 27 neighbours span [-2-b, 3-b] per axis (b the
+// cell's parity on that axis); the 27 near offsets are removed.  Built per
+// CTA in shared memory: il[parity][k] = packed (ox+4) | (oy+4)<<4 | (oz+4)<<8.
+__device__ __forceinline__ void il_table_init(unsigned short (*il)[189]) {
+  for (int t = threadIdx.x; t < 8 * 216; t += blockDim.x) {
+    const int par = t / 216, b = t % 216;
+    const int bx = (par >> 2) & 1, by = (par >> 1) & 1, bz = par & 1;
+    const int i = b / 36, jj = (b / 6) % 6, l = b % 6;
+    const int ox = i - 2 - bx, oy = jj - 2 - by, oz = l - 2 - bz;
+    const bool inner = (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1);
+    if (inner) continue;
+    // rank of b among the non-inner entries of this parity class
+    int k = 0;
+    for (int bb = 0; bb < b; bb++) {
+      const int ii = bb / 36, j2 = (bb / 6) % 6, l2 = bb % 6;
+      const int px = ii - 2 - bx, py = j2 - 2 - by, pz = l2 - 2 - bz;
+      if (!(px >= -1 && px <= 1 && py >= -1 && py <= 1 && pz >= -1 && pz <= 1)) k++;
+    }
+    il[par][k] = (unsigned short)((ox + 4) | ((oy + 4) << 4) | ((oz + 4) << 8));
+  }
+}
+__device__ __forceinline__ void il_unpack(unsigned short v, int* ox, int* oy, int* oz) {
+  *ox = (int)(v & 15) - 4;
+  *oy = (int)((v >> 4) & 15) - 4;
+  *oz = (int)((v >> 8) & 15) - 4;
+}
+
+__device__ __forceinline__ int mc_wrap_coord(int e, int n) { return ((e % n) + n) % n; }
+
+__device__ __forceinline__ bool in_il(int ox, int oy, int oz, int cx, int cy, int cz) {
+  const int bx = cx & 1, by = cy & 1, bz = cz & 1;
+  if (ox < -2 - bx || ox > 3 - bx || oy < -2 - by || oy > 3 - by || oz < -2 - bz || oz > 3 - bz)
+    return false;
+  return (ox < -1 || ox > 1 || oy < -1 || oy > 1 || oz < -1 || oz > 1);
+}
+
+__device__ __forceinline__ int finest_coord(double x, double inv_w, int nL) {
+  int v = (int)floor(__dmul_rn(x, inv_w));
+  return v < 0 ? 0 : (v > nL - 1 ? nL - 1 : v);
+}
+
+// 32-byte record loaded through L2 only (state written by other CTAs)
+__device__ __forceinline__ double4 ldcg4(const double4* p) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+  const double2 a = __ldcg(q), b = __ldcg(q + 1);
+  return make_double4(a.x, a.y, b.x, b.y);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T half_sum(T v) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}

@@ -1,0 +1,543 @@
+// Setup-side kernels: cell lists, Alg. L.3 (initialise the level local
+// expansions) as a per-target gather, the box multipole K and lattice local
+// expansion H = R(K) of Sec. 3.3 (ii)/(iv), the total energy, and the lattice
+// sums / far-field operator behind R.  All FP64.
+#include <math.h>
+
+#include "mc_dev.cuh"
+
+// ---------------------------------------------------------------- cell lists
+__global__ void k_cell_count(int n, const double4* __restrict__ ppos, double inv_w, int nL,
+                             int* __restrict__ cell_of, int* __restrict__ counts) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double4 v = ppos[i];
+    const int cx = finest_coord(v.x, inv_w, nL), cy = finest_coord(v.y, inv_w, nL),
+              cz = finest_coord(v.z, inv_w, nL);
+    const int c = (cx * nL + cy) * nL + cz;
+    cell_of[i] = c;
+    atomicAdd(&counts[c], 1);
+  }
+}
+
+__global__ void k_cell_fill(int n, const int* __restrict__ cell_of, int cap, int* __restrict__ fill,
+                            int* __restrict__ cpid) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int c = cell_of[i];
+    const int s = atomicAdd(&fill[c], 1);
+    cpid[(size_t)c * cap + s] = i;
+  }
+}
+
+// per cell: order the slots by particle id (deterministic layout), then
+// write slot positions (absolute FP64 and FP32 relative to the cell centre)
+__global__ void k_cell_sort(int ncell, int nL, int cap, double w, const int* __restrict__ counts,
+                            const double4* __restrict__ ppos, int* __restrict__ cpid,
+                            double4* __restrict__ cpos, float4* __restrict__ cpos32,
+                            int* __restrict__ pslot) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
+    int* ids = cpid + (size_t)c * cap;
+    const int cnt = counts[c];
+    for (int a = 1; a < cnt; a++) {
+      const int v = ids[a];
+      int b = a - 1;
+      while (b >= 0 && ids[b] > v) {
+        ids[b + 1] = ids[b];
+        b--;
+      }
+      ids[b + 1] = v;
+    }
+    const int cx = c / (nL * nL), cy = (c / nL) % nL, cz = c % nL;
+    const double Rx = (cx + 0.5) * w, Ry = (cy + 0.5) * w, Rz = (cz + 0.5) * w;
+    for (int a = 0; a < cnt; a++) {
+      const int i = ids[a];
+      const double4 v = ppos[i];
+      cpos[(size_t)c * cap + a] = v;
+      cpos32[(size_t)c * cap + a] =
+          make_float4((float)(v.x - Rx), (float)(v.y - Ry), (float)(v.z - Rz), (float)v.w);
+      pslot[i] = c * cap + a;
+    }
+  }
+}
+
+__global__ void k_max_int(int n, const int* __restrict__ v, int* __restrict__ out) {
+  int m = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    m = max(m, v[i]);
+  atomicMax(out, m);
+}
+
+// -------------------------------------------- Alg. L.3 as a per-target gather
+// Each warp task is (target cell t of level l, chunk of t's interaction
+// list).  By the symmetry of the interaction list, the cells whose lists
+// contain t are exactly t's own list (with the opposite image shift), so
+//   Lhat_t = sum_{e in IL(t)} sum_{i in cell(e)} q_i conj It(r_i + shift a - R_t).
+// Two particles per warp step (one per half-warp, lane = column m).
+// Partial expansions of the chunks go to `out` ([t][chunk][C]), reduced in a
+// fixed order by k_reduce_chunks.
+__global__ void __launch_bounds__(MC_THREADS)
+    k_p2l_level(const McSys* __restrict__ sysp, int l, int nchunk, double* __restrict__ out) {
+  __shared__ McSys S;
+  __shared__ HarmTabs<double> tabs;
+  __shared__ unsigned short il[8][189];
+  __shared__ double stage[MC_WARPS][256];
+  if (threadIdx.x == 0) S = *sysp;
+  harm_tabs_init<double>(&tabs);
+  il_table_init(il);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane >> 4, m = lane & 15;
+  const int p = S.p, C = S.C, L = S.L;
+  const bool pbc = S.bc == 0;
+  const int nl = S.lev_n[l], f = 1 << (L - l), nL = S.nL;
+  const double w = S.lev_w[l];
+  const int ntask = nl * nl * nl * nchunk;
+  const int per = (189 + nchunk - 1) / nchunk;
+  for (int task = blockIdx.x * MC_WARPS + warp; task < ntask; task += gridDim.x * MC_WARPS) {
+    const int t = task / nchunk, ch = task % nchunk;
+    const int tc[3] = {t / (nl * nl), (t / nl) % nl, t % nl};
+    const int par = ((tc[0] & 1) << 2) | ((tc[1] & 1) << 1) | (tc[2] & 1);
+    const double Rt[3] = {(tc[0] + 0.5) * w, (tc[1] + 0.5) * w, (tc[2] + 0.5) * w};
+    double ar[MC_PMAX + 1], ai[MC_PMAX + 1];
+#pragma unroll
+    for (int n = 0; n <= MC_PMAX; n++) ar[n] = ai[n] = 0.0;
+    const int kb = ch * per, ke = min(189, kb + per);
+    for (int k = kb; k < ke; k++) {
+      int ox, oy, oz;
+      il_unpack(il[par][k], &ox, &oy, &oz);
+      const int e[3] = {tc[0] + ox, tc[1] + oy, tc[2] + oz};
+      int src[3];
+      double shift[3];
+      bool ok = true;
+      for (int d = 0; d < 3; d++) {
+        if (pbc) {
+          src[d] = mc_wrap_coord(e[d], nl);
+        } else {
+          src[d] = e[d];
+          if (e[d] < 0 || e[d] >= nl) ok = false;
+        }
+        shift[d] = (double)((e[d] - src[d]) / nl) * S.a;
+      }
+      if (!ok) continue;
+      // the finest cells inside the source cell
+      for (int fc = 0; fc < f * f * f; fc++) {
+        const int gx = src[0] * f + fc / (f * f), gy = src[1] * f + (fc / f) % f,
+                  gz = src[2] * f + fc % f;
+        const int cell = (gx * nL + gy) * nL + gz;
+        const int cnt = S.ccount[cell];
+        for (int s0 = 0; s0 < cnt; s0 += 2) {
+          const int s = s0 + half;
+          const bool act = s < cnt;
+          double4 v = make_double4(0, 0, 0, 0);
+          if (act) v = S.cpos[(size_t)cell * S.cap + s];
+          const double dx = act ? v.x + shift[0] - Rt[0] : 3.0;
+          const double dy = act ? v.y + shift[1] - Rt[1] : 3.0;
+          const double dz = act ? v.z + shift[2] - Rt[2] : 3.0;
+          const double qi = act ? v.w : 0.0;
+          irregular_columns<double>(&tabs, p, m, dx, dy, dz, [&](int n, double cr, double ci) {
+            ar[n] += qi * cr;
+            ai[n] -= qi * ci;
+          });
+        }
+      }
+    }
+    double* st = stage[warp];
+#pragma unroll
+    for (int n = 0; n <= MC_PMAX; n++) {
+      const double orr = __shfl_xor_sync(0xffffffffu, ar[n], 16);
+      const double oii = __shfl_xor_sync(0xffffffffu, ai[n], 16);
+      if (half == 0 && n <= p && m <= n) {
+        const int kk = rl_re(n, m);
+        st[kk] = ar[n] + orr;
+        if (m) st[kk + 1] = ai[n] + oii;
+      }
+    }
+    __syncwarp();
+    double* o = out + ((size_t)t * nchunk + ch) * C;
+    for (int kk = lane; kk < C; kk += 32) o[kk] = st[kk];
+    __syncwarp();
+  }
+}
+
+// out[t][k] = sum over chunks in order
+__global__ void k_reduce_chunks(int ntarget, int nchunk, int C, const double* __restrict__ in,
+                                double* __restrict__ out) {
+  const size_t total = (size_t)ntarget * C;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const size_t t = i / C, k = i % C;
+    double s = 0.0;
+    for (int ch = 0; ch < nchunk; ch++) s += in[(t * nchunk + ch) * C + k];
+    out[i] = s;
+  }
+}
+
+// ------------------------------------------- K (Sec. 3.3 ii) and the dipole
+// chunk ch of the particles: partial Khat = sum q conj Rt(r - R1); dipole
+// sum q r appended at [C .. C+2].
+__global__ void __launch_bounds__(MC_THREADS)
+    k_box_multipole(const McSys* __restrict__ sysp, int nchunk, double* __restrict__ out) {
+  __shared__ McSys S;
+  __shared__ HarmTabs<double> tabs;
+  __shared__ double stage[MC_WARPS][256];
+  if (threadIdx.x == 0) S = *sysp;
+  harm_tabs_init<double>(&tabs);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane >> 4, m = lane & 15;
+  const int p = S.p, C = S.C;
+  const int per = (S.n + nchunk - 1) / nchunk;
+  const double c1 = 0.5 * S.a;
+  for (int ch = blockIdx.x * MC_WARPS + warp; ch < nchunk; ch += gridDim.x * MC_WARPS) {
+    double ar[MC_PMAX + 1], ai[MC_PMAX + 1];
+#pragma unroll
+    for (int n = 0; n <= MC_PMAX; n++) ar[n] = ai[n] = 0.0;
+    double D[3] = {0, 0, 0};
+    const int ib = ch * per, ie = min(S.n, ib + per);
+    for (int i0 = ib; i0 < ie; i0 += 2) {
+      const int i = i0 + half;
+      const bool act = i < ie;
+      double4 v = make_double4(c1, c1, c1, 0.0);
+      if (act) v = S.ppos[i];
+      regular_columns<double>(&tabs, p, m, v.x - c1, v.y - c1, v.z - c1,
+                              [&](int n, double cr, double ci) {
+                                ar[n] += v.w * cr;
+                                ai[n] -= v.w * ci;
+                              });
+      if (m == 0) {
+        D[0] += v.w * v.x;
+        D[1] += v.w * v.y;
+        D[2] += v.w * v.z;
+      }
+    }
+    double* st = stage[warp];
+#pragma unroll
+    for (int n = 0; n <= MC_PMAX; n++) {
+      const double orr = __shfl_xor_sync(0xffffffffu, ar[n], 16);
+      const double oii = __shfl_xor_sync(0xffffffffu, ai[n], 16);
+      if (half == 0 && n <= p && m <= n) {
+        const int kk = rl_re(n, m);
+        st[kk] = ar[n] + orr;
+        if (m) st[kk + 1] = ai[n] + oii;
+      }
+    }
+    for (int d = 0; d < 3; d++) D[d] += __shfl_xor_sync(0xffffffffu, D[d], 16);
+    __syncwarp();
+    double* o = out + (size_t)ch * (C + 3);
+    for (int kk = lane; kk < C; kk += 32) o[kk] = st[kk];
+    if (lane == 0) {
+      o[C] = D[0];
+      o[C + 1] = D[1];
+      o[C + 2] = D[2];
+    }
+    __syncwarp();
+  }
+}
+
+// Khat, dipole from the chunk partials (fixed order), then Hhat = G Khat
+__global__ void k_far_finish(const McSys* __restrict__ sysp, int nchunk,
+                             const double* __restrict__ in) {
+  const McSys& S = *sysp;
+  const int C = S.C;
+  __shared__ double kh[256 + 3];
+  for (int k = threadIdx.x; k < C + 3; k += blockDim.x) {
+    double s = 0.0;
+    for (int ch = 0; ch < nchunk; ch++) s += in[(size_t)ch * (C + 3) + k];
+    kh[k] = s;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < C; k += blockDim.x) {
+    S.Khat[k] = kh[k];
+    double h = 0.0;
+    if (S.bc == 0)
+      for (int c = 0; c < C; c++) h += S.G[(size_t)c * C + k] * kh[c];
+    S.Hhat[k] = h;
+  }
+  if (threadIdx.x < 3) S.dipv[threadIdx.x] = kh[C + threadIdx.x];
+}
+
+// ------------------------------------------------------------ total energy
+// U = 1/2 sum_i q_i phi_i + 1/2 sum_k W_k Khat_k Hhat_k + dipole term, where
+// phi_i sums the level expansions at r_i and the direct near-cell charges
+// other than i itself.  One warp per particle; per-warp running sums in
+// `out` (fixed assignment), reduced by k_energy_finish.
+__global__ void __launch_bounds__(MC_THREADS)
+    k_energy_particles(const McSys* __restrict__ sysp, double* __restrict__ out) {
+  __shared__ McSys S;
+  __shared__ HarmTabs<double> tabs;
+  if (threadIdx.x == 0) S = *sysp;
+  harm_tabs_init<double>(&tabs);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane >> 4, m = lane & 15;
+  const int p = S.p, C = S.C, L = S.L, nL = S.nL;
+  const bool pbc = S.bc == 0;
+  const int gw = blockIdx.x * MC_WARPS + warp, nw = gridDim.x * MC_WARPS;
+  double usum = 0.0;
+  for (int i = gw; i < S.n; i += nw) {
+    const double4 v = S.ppos[i];
+    const int cf[3] = {finest_coord(v.x, S.inv_wL, nL), finest_coord(v.y, S.inv_wL, nL),
+                       finest_coord(v.z, S.inv_wL, nL)};
+    double phi = 0.0;
+    // level expansions: two levels per warp step (one per half-warp)
+    const int nlev = L - S.lmin + 1;
+    for (int l0 = 0; l0 < nlev; l0 += 2) {
+      const int li = l0 + half;
+      const bool act = li < nlev;
+      const int l = act ? L - li : L;
+      const int sh = L - l, nl = S.lev_n[l];
+      const double w = S.lev_w[l];
+      const int cx = cf[0] >> sh, cy = cf[1] >> sh, cz = cf[2] >> sh;
+      const double* Lb = S.Lhat + (size_t)(S.lev_off[l] + (cx * nl + cy) * nl + cz) * C;
+      double Lr[MC_PMAX + 1], Li[MC_PMAX + 1];
+#pragma unroll
+      for (int n = 0; n <= MC_PMAX; n++) {
+        Lr[n] = Li[n] = 0.0;
+        if (act && n <= p && m <= n) {
+          const int k = rl_re(n, m);
+          Lr[n] = Lb[k];
+          if (m) Li[n] = Lb[k + 1];
+        }
+      }
+      double acc = 0.0;
+      regular_columns<double>(&tabs, p, m, v.x - (cx + 0.5) * w, v.y - (cy + 0.5) * w,
+                              v.z - (cz + 0.5) * w, [&](int n, double cr, double ci) {
+                                if (n >= m) acc += Lr[n] * cr - Li[n] * ci;
+                              });
+      if (m > p || !act) acc = 0.0;
+      if (m > 0) acc *= 2.0;
+      phi += acc;
+    }
+    // direct near cells
+    for (int k = 0; k < 27; k++) {
+      const int e0 = cf[0] + k / 9 - 1, e1 = cf[1] + (k / 3) % 3 - 1, e2 = cf[2] + k % 3 - 1;
+      int c0 = e0, c1 = e1, c2 = e2;
+      if (pbc) {
+        c0 = mc_wrap_coord(e0, nL);
+        c1 = mc_wrap_coord(e1, nL);
+        c2 = mc_wrap_coord(e2, nL);
+      } else if (e0 < 0 || e0 >= nL || e1 < 0 || e1 >= nL || e2 < 0 || e2 >= nL) {
+        continue;
+      }
+      const double sx = ((e0 - c0) / nL) * S.a, sy = ((e1 - c1) / nL) * S.a,
+                   sz = ((e2 - c2) / nL) * S.a;
+      const bool zs = (e0 == c0 && e1 == c1 && e2 == c2);
+      const int cell = (c0 * nL + c1) * nL + c2;
+      const int cnt = S.ccount[cell];
+      for (int s = lane; s < cnt; s += 32) {
+        const int pid = S.cpid[(size_t)cell * S.cap + s];
+        if (pid == i && zs) continue;
+        const double4 xi = S.cpos[(size_t)cell * S.cap + s];
+        const double ax = v.x - (xi.x + sx), ay = v.y - (xi.y + sy), az = v.z - (xi.z + sz);
+        phi += xi.w * rsqrt(ax * ax + ay * ay + az * az);
+      }
+    }
+    phi = warp_sum(phi);
+    usum += 0.5 * v.w * phi;
+  }
+  if (lane == 0) out[gw] = usum;
+}
+
+__global__ void k_energy_finish(const McSys* __restrict__ sysp, int nw, const double* __restrict__ in,
+                                double* __restrict__ dst) {
+  const McSys& S = *sysp;
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nw; i += blockDim.x) s += in[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double U = red[0];
+    if (S.bc == 0) {
+      double far = 0.0;
+      for (int k = 0; k < S.C; k++) {
+        const int r = (int)sqrtf((float)k + 0.5f);
+        far += ((r * r == k) ? 1.0 : 2.0) * S.Khat[k] * S.Hhat[k];
+      }
+      U += 0.5 * far;
+      if (S.dip == 0) {
+        const double D2 = S.dipv[0] * S.dipv[0] + S.dipv[1] * S.dipv[1] + S.dipv[2] * S.dipv[2];
+        U += -2.0 * 3.141592653589793 / (3.0 * S.V) * D2;
+      }
+    }
+    dst[0] = U;
+  }
+}
+
+// ------------------------------------------------------------ lattice sums
+// Scaled lattice sums St_l^mu = sum_{max|v_i| >= 2} It_l^mu(v) over the unit
+// lattice (It the scaled irregular harmonic; St = s_l,mu S_l^mu).  Images are
+// summed in cubic shells: l = 1, 2 vanish by cubic symmetry and l = 0 only
+// meets the total charge (zero), so l < 3 is 0.  For 3 <= l < 14 the sum
+// over all v != 0 is split (Poisson summation of the harmonic polynomial
+// h(x) = |x|^l Y(x), split at t = 2):
+//   sum_v h(v)/|v|^(2l+1) Q(l+1/2, 2 pi |v|^2)
+//   + pi^(l-1/2)/Gamma(l+1/2) (-i)^l sum_{k != 0} h(k) e^{-pi |k|^2 / 2} / |k|^2
+// and the 26 shell-1 terms are removed.  For l >= 14 shells 2..32 are summed
+// directly (tail below 1e-15 relative).  One block per (l, mu >= 0).
+__device__ __forceinline__ void rt_single(int l, int mu, double x, double y, double z,
+                                          double* re, double* im) {
+  // scaled regular harmonic Rt_l^mu(x) via the diagonal then the column
+  double dr = 1.0, di = 0.0;
+  for (int k = 1; k <= mu; k++) {
+    const double nr = (dr * x - di * y) / (2.0 * k), ni = (dr * y + di * x) / (2.0 * k);
+    dr = nr;
+    di = ni;
+  }
+  const double r2 = x * x + y * y + z * z;
+  double p1r = dr, p1i = di, p2r = 0.0, p2i = 0.0;
+  for (int n = mu + 1; n <= l; n++) {
+    const double den = (double)(n + mu) * (double)(n - mu);
+    const double a = (2.0 * n - 1.0) * z / den, b = r2 / den;
+    const double cr = a * p1r - b * p2r, ci = a * p1i - b * p2i;
+    p2r = p1r;
+    p2i = p1i;
+    p1r = cr;
+    p1i = ci;
+  }
+  *re = p1r;
+  *im = p1i;
+}
+
+__global__ void k_lattice_sums(int lmax, double* __restrict__ out /* complex (lmax+1)^2 */) {
+  // block -> (l, mu)
+  int b = blockIdx.x, l = 0;
+  while (b >= l + 1) {
+    b -= l + 1;
+    l++;
+  }
+  const int mu = b;
+  __shared__ double rr[256], ri[256];
+  double sr = 0.0, si = 0.0;
+  double fl = 1.0, fh = 1.0;  // (l-mu)!, (l+mu)!
+  for (int k = 2; k <= l - mu; k++) fl *= k;
+  for (int k = 2; k <= l + mu; k++) fh *= k;
+  const double s2 = fl * fh;  // h = s2 * Rt
+  const double pi = 3.141592653589793;
+  if (l >= 3 && l < 14) {
+    const int R = 7, K = 9;
+    const int side = 2 * R + 1;
+    for (int idx = threadIdx.x; idx < side * side * side; idx += blockDim.x) {
+      const int x = idx / (side * side) - R, y = (idx / side) % side - R, z = idx % side - R;
+      if (!x && !y && !z) continue;
+      const double r2 = (double)(x * x + y * y + z * z), r = sqrt(r2);
+      double hr, hi;
+      rt_single(l, mu, x, y, z, &hr, &hi);
+      hr *= s2;
+      hi *= s2;
+      // Q(l + 1/2, 2 pi r^2)
+      const double X = 2.0 * pi * r2;
+      double Q = erfc(sqrt(X));
+      double term = sqrt(X) * exp(-X) / (0.5 * sqrt(pi));  // x^{1/2} e^-x / Gamma(3/2)
+      for (int i = 0; i < l; i++) {
+        Q += term;
+        term *= X / (i + 1.5);
+      }
+      double wgt = Q;
+      if (abs(x) <= 1 && abs(y) <= 1 && abs(z) <= 1) wgt -= 1.0;
+      const double inv = pow(r, -(2.0 * l + 1.0));
+      sr += hr * wgt * inv;
+      si += hi * wgt * inv;
+    }
+    // reciprocal part
+    double gam = sqrt(pi);
+    for (int i = 0; i < l; i++) gam *= (0.5 + i);
+    const double pref = pow(pi, l - 0.5) / gam;
+    // (-i)^l
+    const int lm = l & 3;
+    const double ur = (lm == 0) ? 1.0 : (lm == 2 ? -1.0 : 0.0);
+    const double ui = (lm == 1) ? -1.0 : (lm == 3 ? 1.0 : 0.0);
+    const int sk = 2 * K + 1;
+    for (int idx = threadIdx.x; idx < sk * sk * sk; idx += blockDim.x) {
+      const int x = idx / (sk * sk) - K, y = (idx / sk) % sk - K, z = idx % sk - K;
+      if (!x && !y && !z) continue;
+      const double k2 = (double)(x * x + y * y + z * z);
+      double hr, hi;
+      rt_single(l, mu, x, y, z, &hr, &hi);
+      const double wgt = pref * s2 * exp(-pi * k2 / 2.0) / k2;
+      sr += wgt * (ur * hr - ui * hi);
+      si += wgt * (ur * hi + ui * hr);
+    }
+  } else if (l >= 14) {
+    const int R = 32, side = 2 * R + 1;
+    for (int idx = threadIdx.x; idx < side * side * side; idx += blockDim.x) {
+      const int x = idx / (side * side) - R, y = (idx / side) % side - R, z = idx % side - R;
+      if (max(abs(x), max(abs(y), abs(z))) < 2) continue;
+      const double r2 = (double)(x * x + y * y + z * z);
+      double hr, hi;
+      rt_single(l, mu, x, y, z, &hr, &hi);
+      const double inv = pow(r2, -(l + 0.5));
+      sr += s2 * hr * inv;
+      si += s2 * hi * inv;
+    }
+  }
+  rr[threadIdx.x] = sr;
+  ri[threadIdx.x] = si;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      rr[threadIdx.x] += rr[threadIdx.x + o];
+      ri[threadIdx.x] += ri[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int id = l * l + l + mu;
+    out[2 * id] = rr[0];
+    out[2 * id + 1] = ri[0];
+    if (mu > 0) {
+      const int idn = l * l + l - mu;
+      out[2 * idn] = rr[0];
+      out[2 * idn + 1] = -ri[0];
+    }
+  }
+}
+
+// --------------------------------------------------- far-field operator G
+// Hhat = G Khat in the scaled real layout.  The multipole-to-local theorem
+// of Greengard and Rokhlin, written for the scaled expansions, becomes
+//   Hhat_j^k = sum_{n, m=-n..n} (-1)^n sigma(k, m) a^-(j+n+1) St_{j+n}^{m-k} Khat_n^m
+// with sigma(k, m) = i^{|k-m|-|k|-|m|} (a real sign), Khat_n^-m = conj Khat_n^m
+// and St the scaled lattice sums.  One thread per matrix entry; stored
+// column-major: G[c * C + row].
+__device__ __forceinline__ void rl_decode(int k, int* n, int* m, int* im) {
+  int r = (int)sqrtf((float)k + 0.5f);
+  while (r * r > k) r--;
+  while ((r + 1) * (r + 1) <= k) r++;
+  *n = r;
+  const int rem = k - r * r;
+  *m = (rem + 1) / 2;
+  *im = (rem > 0 && (rem % 2) == 0) ? 1 : 0;
+}
+
+__device__ __forceinline__ double sigma_km(int k, int m) {
+  const int e = (abs(k) + abs(m) - abs(k - m)) / 2;
+  return (e & 1) ? -1.0 : 1.0;
+}
+
+__global__ void k_far_operator(int p, double a, const double* __restrict__ St, double* __restrict__ G) {
+  const int C = (p + 1) * (p + 1);
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < C * C; idx += gridDim.x * blockDim.x) {
+    const int c = idx / C, row = idx % C;
+    int j, k, rim, n, m, cim;
+    rl_decode(row, &j, &k, &rim);
+    rl_decode(c, &n, &m, &cim);
+    const int l = j + n;
+    const double sc = ((n & 1) ? -1.0 : 1.0) * pow(a, -(double)(l + 1));
+    // T1 multiplies Khat_n^m, T2 multiplies conj(Khat_n^m) (the -m term)
+    const int mu1 = m - k, mu2 = -m - k;
+    const double s1 = sigma_km(k, m) * sc, s2 = sigma_km(k, -m) * sc;
+    const double t1r = s1 * St[2 * (l * l + l + mu1)], t1i = s1 * St[2 * (l * l + l + mu1) + 1];
+    double t2r = 0.0, t2i = 0.0;
+    if (m > 0) {
+      t2r = s2 * St[2 * (l * l + l + mu2)];
+      t2i = s2 * St[2 * (l * l + l + mu2) + 1];
+    }
+    double v;
+    if (!rim && !cim) v = t1r + t2r;
+    else if (!rim && cim) v = -(t1i - t2i);
+    else if (rim && !cim) v = t1i + t2i;
+    else v = t1r - t2r;
+    G[idx] = v;
+  }
+}
