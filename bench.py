@@ -1,0 +1,361 @@
+"""Benchmark: Metropolis-Hastings steps per second of the multilevel
+local-expansion electrostatics method on the uniform N=1e5 workload
+(density 0.1, a=100, 5 levels, p=12, h=0.3, beta=1).
+
+One bench step = one persistent launch (mc_run) of --mh-steps proposals on
+the resident system.  `value` is the FP64 form, timed with CUDA events on the
+library's stream, L2 flushed between timed steps.  The JSON line also carries
+the FP32-eval form, the setup time, the end-to-end number through the C ABI
+with host buffers, the roofline of the chain kernel and the CPU oracle
+baseline.  --impl reference times the CPU oracle instead.
+
+Multi-GPU: independent replicas (one chain per GPU, seed = rank), no
+collective on the data path; value = all ranks' proposals / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MH steps/sec at N=1e5, p=12: plain FP64 vs FP32-eval/FP64-acc and batched"
+UNIT = "MH steps/s"
+FP64_PEAK_FLOPS = 152 * 4 * 2.070e9  # 152 SMs x 4 FP64 flop/clk/SM (2 FMA lanes) x max clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mh-steps", type=int, default=50_000, help="proposals per bench step")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=3000, help="oracle proposals timed")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------- CPU oracle leg
+def _oracle_worker(q_out, sample, warm):
+    """Runs in a spawned process: oracle setup (untimed), then `sample`
+    proposals of the same chain timed on one host core."""
+    import numpy as np  # noqa: F401
+
+    import oracle
+    from paper_2006_16622_gb300.workloads import LARGE
+    pos, q = LARGE.system()
+    t0 = time.perf_counter()
+    s = oracle.System(pos, q, LARGE.a, LARGE.levels, LARGE.p)
+    s.setup()
+    t_setup = time.perf_counter() - t0
+    s.run(warm, seed=LARGE.seed, step0=0, beta=LARGE.beta, half_width=LARGE.half_width, log=False)
+    t0 = time.perf_counter()
+    r = s.run(sample, seed=LARGE.seed, step0=warm, beta=LARGE.beta, half_width=LARGE.half_width,
+              log=False)
+    dt = time.perf_counter() - t0
+    q_out.put(dict(value=sample / dt, setup_s=t_setup, n_acc=r["n_acc"], sample=sample, secs=dt))
+
+
+def start_oracle(sample, warm=100):
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=_oracle_worker, args=(q, sample, warm), daemon=True)
+    p.start()
+    return p, q
+
+
+def cpu_baseline_from(res):
+    return {"value": res["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"{res['sample']} proposals (after 100 warm-up) of the same chain on the "
+                       f"N=1e5 workload, FP64 oracle, one host thread; oracle setup "
+                       f"{res['setup_s']:.0f} s not timed")}
+
+
+def reference_arm(args):
+    import torch.distributed as dist  # noqa: F401
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2006_16622_gb300.workloads import LARGE
+    oracle.build()
+    pos, q = LARGE.system()
+    t0 = time.perf_counter()
+    s = oracle.System(pos, q, LARGE.a, LARGE.levels, LARGE.p)
+    s.setup()
+    setup_s = time.perf_counter() - t0
+    per = 500
+    step = 0
+    for _ in range(args.warmup):
+        s.run(per, seed=LARGE.seed, step0=step, beta=LARGE.beta, half_width=LARGE.half_width,
+              log=False)
+        step += per
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        s.run(per, seed=LARGE.seed, step0=step, beta=LARGE.beta, half_width=LARGE.half_width,
+              log=False)
+        times.append(time.perf_counter() - t0)
+        step += per
+    tot = sum(times)
+    v = per * args.steps / tot
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": LARGE.name, "mh_steps_per_step": per, "form": "fp64"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{per} proposals per step of the N=1e5 chain, one host "
+                                       f"thread; setup {setup_s:.0f} s not timed"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, fl in rows for i, v in enumerate(fl)
+                          if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def algorithmic_flops_per_step(p, levels, nbar, nu):
+    """FP64 flops of one MH step from the algorithm (not the implementation):
+    a solid-harmonic set 3(p+1)(p+2) flops; an expansion evaluation adds a
+    2C dot product; a near-field pair 11 flops; the far lattice term two
+    harmonic sets and the dense operator (2C^2); an accept 2*189 P2L sets and
+    one C-length update per interaction-list cell and level."""
+    C = (p + 1) ** 2
+    hset = 3 * (p + 1) * (p + 2)
+    L_eff = levels - 1
+    f_prop = 2 * L_eff * (hset + 2 * C) + 2 * 27 * nbar * 11 + 2 * hset + 2 * C * C + 4 * C + 27 * 11
+    f_acc = 2 * 189 * L_eff * (hset + 2 * C) + 189 * L_eff * C + 4 * C
+    return f_prop + nu * f_acc, f_prop, f_acc
+
+
+def bytes_per_step(p, levels, nbar, nu):
+    C = (p + 1) ** 2
+    L_eff = levels - 1
+    b_prop = 2 * L_eff * C * 8 + 2 * 27 * nbar * 36 + C * C * 8 + 2 * C * 8
+    b_acc = 2 * 189 * L_eff * C * 8 + 4 * C * 8
+    return b_prop + nu * b_acc
+
+
+def read_profile_traffic():
+    """DRAM bytes per MH step of the chain kernel from the committed ncu summary."""
+    path = os.path.join(ROOT, "profiles", "chain_fp64_uniform_N1e5.md")
+    try:
+        for line in open(path):
+            if line.startswith("dram_bytes_per_mh_step:"):
+                return float(line.split(":")[1])
+    except OSError:
+        pass
+    return None
+
+
+def gpu_arm(args):
+    import numpy as np
+    import torch
+
+    from paper_2006_16622_gb300 import mcfmm
+    from paper_2006_16622_gb300.workloads import LARGE
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    oracle_proc = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        oracle_proc = start_oracle(args.cpu_sample)
+
+    mcfmm.load()
+    stream = torch.cuda.current_stream()
+    W = LARGE
+    pos, q = W.system()
+    S = args.mh_steps
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def time_form(precision):
+        ctx = mcfmm.Context(pos, q, W.a, W.levels, W.p, precision=precision,
+                            stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.setup()
+        setup_s = time.perf_counter() - t0
+        seed = W.seed + 1000 * rank
+        for _ in range(args.warmup):
+            ctx.run(S, seed=seed, beta=W.beta, half_width=W.half_width, stats=False)
+        torch.cuda.synchronize()
+        durs = []
+        sampler = ClockSampler(local)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        sampler.start()
+        for _ in range(args.steps):
+            flush.zero_()  # write 256 MiB (> 129 MB L2) between timed steps
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.run(S, seed=seed, beta=W.beta, half_width=W.half_width, stats=False)
+            e1.record(stream)
+            e1.synchronize()
+            durs.append(e0.elapsed_time(e1) / 1000.0)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        if dist is not None:
+            dist.barrier()
+        # acceptance rate over a stats-reporting run of the same chain
+        st = ctx.run(min(S, 20_000), seed=seed, beta=W.beta, half_width=W.half_width)
+        nu = st["accepted"] / max(1, st["steps"])
+        status = ctx.status()
+        ctx.close()
+        if status != 0:
+            raise RuntimeError(f"chain status {status}")
+        tot = sum(durs)
+        if dist is not None:
+            t = torch.tensor([tot], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot = float(t.item())
+        return dict(total=tot, durs=durs, setup_s=setup_s, nu=nu, clocks=clocks)
+
+    r64 = time_form(mcfmm.FP64)
+    r32 = None if args.no_fp32 else time_form(mcfmm.FP32_EVAL)
+
+    # end to end through the C ABI: host arrays in, positions and energy out
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t_e2e = []
+        for i in range(2):
+            t0 = time.perf_counter()
+            ctx = mcfmm.Context(pos, q, W.a, W.levels, W.p, precision=mcfmm.FP64,
+                                stream=stream.cuda_stream)
+            ctx.setup()
+            ctx.run(S, seed=W.seed + 7 + 1000 * rank, beta=W.beta, half_width=W.half_width,
+                    stats=False)
+            out_pos = ctx.positions()
+            e = ctx.energy()
+            ctx.close()
+            t_e2e.append(time.perf_counter() - t0)
+            assert np.isfinite(e) and out_pos.shape == pos.shape
+        te = max(t_e2e[1:]) if len(t_e2e) > 1 else t_e2e[0]
+        e2e = {"value": world * S / te, "unit": UNIT,
+               "h2d_bytes_per_step": int(pos.nbytes + q.nbytes),
+               "d2h_bytes_per_step": int(len(q) * 32 + 8),
+               "what": "per step: mc_init from host arrays, mc_setup, mc_run, positions + energy "
+                       "copied back, mc_destroy"}
+
+    if rank != 0:
+        return
+    value = world * S * args.steps / r64["total"]
+    nbar = W.n / (8 ** (W.levels - 1))
+    F, Fp, Fa = algorithmic_flops_per_step(W.p, W.levels, nbar, r64["nu"])
+    per_launch = statistics.mean(r64["durs"])
+    achieved = F * S / per_launch
+    traffic_per_step = read_profile_traffic()
+    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
+            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_FLOPS,
+            "traffic": (traffic_per_step * S) if traffic_per_step else None,
+            "kernel": "mc_chain_kernel<double>",
+            "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (recipe unit counts)",
+            "flops_per_mh_step": F, "bytes_per_mh_step": bytes_per_step(W.p, W.levels, nbar, r64["nu"]),
+            "acceptance": r64["nu"]}
+    cpu = None
+    if oracle_proc is not None:
+        proc, qq = oracle_proc
+        try:
+            res = qq.get(timeout=900)
+            cpu = cpu_baseline_from(res)
+        except Exception as ex:  # noqa: BLE001
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"oracle leg failed: {ex!r}"}
+        proc.join(timeout=10)
+    forms = {"fp64": value}
+    if r32:
+        forms["fp32_eval"] = world * S * args.steps / r32["total"]
+        forms["fp32_eval_acceptance"] = r32["nu"]
+        forms["fp32_eval_setup_s"] = r32["setup_s"]
+    forms["batched"] = None
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * r64["total"] / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": W.name, "mh_steps_per_step": S, "form": "fp64",
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": args.steps, "clocks": r64["clocks"], "forms": forms,
+            "setup_s": r64["setup_s"]}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -123,6 +123,16 @@ int mc_status(mc_ctx *ctx);
 /* Wait-limit of the device-side grid barrier in nanoseconds (default 2e9);
  * a wait that runs out sets MC_ERR_TIMEOUT and the launch returns. */
 int mc_set_wait_limit(mc_ctx *ctx, int64_t ns);
+/* Diagnostics: with profiling on, mc_run accumulates 32 device timers
+ * (globaltimer nanoseconds) of its persistent launch: [0..4] CTA 0's own
+ * propose items, first barrier wait, decision, own accept items, second
+ * barrier wait; [5] proposals, [6] accepts; [8+t], [16+t], [24+t] summed
+ * duration, count and maximum of work items of type t (0 expansion
+ * evaluation, 1 near cell, 2 far lattice block, 3 image/dipole term,
+ * 4 small-level accept entry, 5 accept target cell, 6 bookkeeping).
+ * mc_profile_read copies them (out: 32 uint64) and clears them. */
+int mc_profile(mc_ctx *ctx, int on);
+int mc_profile_read(mc_ctx *ctx, uint64_t *out);
 void mc_destroy(mc_ctx *ctx);
 const char *mc_strerror(int status);
 

@@ -71,17 +71,36 @@ static void legendre_table(int p, double x, double *P /* [(p+1)*(p+1)] n-major *
   }
 }
 
+#define ORC_PMAX 64
+
+/* sqrt((n-|m|)!/(n+|m|)!) for n <= ORC_PMAX, cached on first use */
+static double ynorm(int n, int am) {
+  static double table[(ORC_PMAX + 1) * (ORC_PMAX + 1)];
+  static int ready = 0;
+  if (!ready) {
+    for (int nn = 0; nn <= ORC_PMAX; nn++)
+      for (int mm = 0; mm <= nn; mm++)
+        table[nn * (ORC_PMAX + 1) + mm] = sqrt(factorial(nn - mm) / factorial(nn + mm));
+    ready = 1;
+  }
+  return table[n * (ORC_PMAX + 1) + am];
+}
+
 static void ylm_table(int p, double theta, double phi, cplx *Y) {
-  double *P = (double *)malloc(sizeof(double) * (p + 1) * (p + 1));
+  double P[(ORC_PMAX + 1) * (ORC_PMAX + 1)];
+  cplx eimp[ORC_PMAX + 1];
   legendre_table(p, cos(theta), P);
+  /* e^{i m phi} for m = 0..p by repeated multiplication */
+  const cplx e1 = cos(phi) + I * sin(phi);
+  eimp[0] = 1.0;
+  for (int m = 1; m <= p; m++) eimp[m] = eimp[m - 1] * e1;
   for (int n = 0; n <= p; n++) {
-    for (int m = -n; m <= n; m++) {
-      int am = m < 0 ? -m : m;
-      double norm = sqrt(factorial(n - am) / factorial(n + am));
-      Y[IDX(n, m)] = norm * P[n * (p + 1) + am] * cexp(I * (double)m * phi);
+    for (int m = 0; m <= n; m++) {
+      const double v = ynorm(n, m) * P[n * (p + 1) + m];
+      Y[IDX(n, m)] = v * eimp[m];
+      if (m) Y[IDX(n, -m)] = v * conj(eimp[m]);
     }
   }
-  free(P);
 }
 
 /* spherical(x) of the paper: (r, theta, phi) */
@@ -123,6 +142,7 @@ static void to_interleaved(int p, const cplx *c, double *out) {
 }
 
 void orc_ylm(int p, double theta, double phi, double *out) {
+  if (p < 0 || p > ORC_PMAX) return;
   cplx *Y = (cplx *)malloc(sizeof(cplx) * (p + 1) * (p + 1));
   ylm_table(p, theta, phi, Y);
   to_interleaved(p, Y, out);
@@ -130,6 +150,7 @@ void orc_ylm(int p, double theta, double phi, double *out) {
 }
 
 void orc_regular(int p, const double x[3], double *out) {
+  if (p < 0 || p > ORC_PMAX) return;
   cplx *Y = (cplx *)malloc(sizeof(cplx) * (p + 1) * (p + 1));
   regular_table(p, x, Y);
   to_interleaved(p, Y, out);
@@ -137,6 +158,7 @@ void orc_regular(int p, const double x[3], double *out) {
 }
 
 void orc_irregular(int p, const double x[3], double *out) {
+  if (p < 0 || p > ORC_PMAX) return;
   cplx *Y = (cplx *)malloc(sizeof(cplx) * (p + 1) * (p + 1));
   irregular_table(p, x, Y);
   to_interleaved(p, Y, out);
@@ -263,8 +285,8 @@ static void lattice_sums_compute(int lmax, double *out);
 
 /* the unit-lattice sums depend only on lmax: computed once per process */
 void orc_lattice_sums(int lmax, double *out) {
-  static double *cache[129];
-  if (lmax < 0 || lmax > 128) return;
+  static double *cache[ORC_PMAX + 1];
+  if (lmax < 0 || lmax > ORC_PMAX) return;
   int C2 = (lmax + 1) * (lmax + 1);
   if (!cache[lmax]) {
     double *t = (double *)malloc(sizeof(double) * 2 * C2);
@@ -352,6 +374,7 @@ struct orc_sys {
   double energy;
   double parts[4];
   cplx *w1, *w2, *w3, *w4;
+  double *m2lf; /* m2l_factor(j,k,n,m), [IDX(j,k)][IDX(n,m)] */
 };
 
 static int ncell_axis(int l) { return 1 << (l - 1); }
@@ -450,7 +473,7 @@ static void cell_list_remove(orc_sys *s, int cell, int64_t i) {
 
 orc_sys *orc_create(int64_t n, const double *pos, const double *q, double a, int levels,
                     int p, int bc, int dipole_bc) {
-  if (levels < 2 || levels > 9 || p < 0 || n < 1) return NULL;
+  if (levels < 2 || levels > 9 || p < 0 || 2 * p > ORC_PMAX || n < 1) return NULL;
   orc_sys *s = (orc_sys *)calloc(1, sizeof(orc_sys));
   s->n = n;
   s->a = a;
@@ -490,6 +513,14 @@ orc_sys *orc_create(int64_t n, const double *pos, const double *q, double a, int
     for (int k = 0; k < (lmax + 1) * (lmax + 1); k++) s->Slat[k] = tmp[2 * k] + I * tmp[2 * k + 1];
     free(tmp);
   }
+  if (bc == ORC_BC_PBC) {
+    s->m2lf = (double *)malloc(sizeof(double) * s->C * s->C);
+    for (int j = 0; j <= p; j++)
+      for (int k = -j; k <= j; k++)
+        for (int n = 0; n <= p; n++)
+          for (int m = -n; m <= n; m++)
+            s->m2lf[(size_t)IDX(j, k) * s->C + IDX(n, m)] = m2l_factor(j, k, n, m);
+  }
   int Cw = (2 * p + 1) * (2 * p + 1);
   s->w1 = (cplx *)malloc(sizeof(cplx) * Cw);
   s->w2 = (cplx *)malloc(sizeof(cplx) * Cw);
@@ -516,6 +547,7 @@ void orc_destroy(orc_sys *s) {
   free(s->w2);
   free(s->w3);
   free(s->w4);
+  free(s->m2lf);
   free(s);
 }
 
@@ -524,13 +556,21 @@ void orc_destroy(orc_sys *s) {
  * translation kernel of one image by its sum over all images outside the
  * extended domain. */
 static void apply_R(const orc_sys *s, const cplx *Kin, cplx *Hout) {
-  int p = s->p, lmax = 2 * p;
+  int p = s->p, lmax = 2 * p, C = s->C;
   cplx *G = s->w4;
   for (int l = 0; l <= lmax; l++) {
     double sc = pow(s->a, -(double)(l + 1));
     for (int m = -l; m <= l; m++) G[IDX(l, m)] = s->Slat[IDX(l, m)] * sc;
   }
-  m2l_apply(p, Kin, G, Hout);
+  /* same sum as m2l_apply, with the translation factors tabulated */
+  for (int j = 0; j <= p; j++)
+    for (int k = -j; k <= j; k++) {
+      const double *f = s->m2lf + (size_t)IDX(j, k) * C;
+      cplx acc = 0.0;
+      for (int n = 0; n <= p; n++)
+        for (int m = -n; m <= n; m++) acc += Kin[IDX(n, m)] * f[IDX(n, m)] * G[IDX(j + n, m - k)];
+      Hout[IDX(j, k)] = acc;
+    }
 }
 
 static const double *R1(const orc_sys *s, double c[3]) {

@@ -44,6 +44,7 @@ struct mc_ctx {
   double* d_scratch;
   size_t scratch_doubles;
   double* d_energy_tmp;  // fresh-energy target
+  unsigned long long* d_prof;  // 32 timers when profiling is on, else null
   std::vector<void*> allocs;
 };
 
@@ -109,6 +110,7 @@ int sync_status(mc_ctx* c) {
 
 int launch_chain(mc_ctx* c, RunParams& rp) {
   rp.wait_ns = c->wait_ns;
+  rp.prof = c->d_prof;
   CK(cudaMemsetAsync(c->h.bar, 0, sizeof(unsigned long long), c->stream));
   CK(cudaMemsetAsync(c->h.status, 0, sizeof(int), c->stream));
   CK(mc_launch_chain(c->d_sys, rp, c->h.prec, c->nCTA, c->stream));
@@ -586,6 +588,28 @@ int mc_lattice_sums(int lmax, double* out) {
       out[2 * (l * l + l + m)] /= s;
       out[2 * (l * l + l + m) + 1] /= s;
     }
+  return MC_OK;
+}
+
+int mc_profile(mc_ctx* c, int on) {
+  if (!c) return MC_ERR_ARG;
+  CK(cudaSetDevice(c->dev));
+  if (on && !c->d_prof) {
+    if (dalloc(c, (void**)&c->d_prof, 32 * sizeof(unsigned long long)) != MC_OK) return MC_ERR_NOMEM;
+    CK(cudaMemset(c->d_prof, 0, 32 * sizeof(unsigned long long)));
+  } else if (!on) {
+    c->d_prof = nullptr;  // the buffer stays owned by the context
+  }
+  return MC_OK;
+}
+
+int mc_profile_read(mc_ctx* c, uint64_t* out) {
+  if (!c || !out) return MC_ERR_ARG;
+  if (!c->d_prof) return MC_ERR_STATE;
+  CK(cudaSetDevice(c->dev));
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(out, c->d_prof, 32 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+  CK(cudaMemset(c->d_prof, 0, 32 * sizeof(unsigned long long)));
   return MC_OK;
 }
 

@@ -3,19 +3,26 @@
 // Sec. 3.3) and Alg. L.2 (accept) for one system on the whole GPU.
 //
 // One step:
-//   1. every thread draws the same Philox proposal (j, r -> r');
+//   1. warp 0 of every CTA draws the same Philox proposal (j, r -> r') and
+//      the offsets of r and r' from the centres of their cells on every
+//      level; the CTA reads them from shared memory;
 //   2. propose items, one warp each, spread over the SMs:
 //        E  level expansions (Eq. 1/2) at r and r' on level l
 //        N  direct sum over one of the 27 near cells (Alg. 1)
-//        F  far lattice term: dK and a 32-row x C/8-column block of G dK
-//        X  image self-interaction correction, dipole term, log(u)
+//        F  far lattice term: dK and a 32-row x C/16-column block of G dK
+//        X  image self-interaction correction and dipole term
+//        U  log(u) of the Metropolis test
 //      each writes one partial sum;
 //   3. grid barrier;
 //   4. every CTA reduces the partials in the same fixed order -> dE and the
 //      Metropolis decision (identical in every CTA, no broadcast needed);
-//   5. on accept: target items (one warp per updated cell of each level's
-//      interaction lists, Alg. L.2) and one bookkeeping item (K, H, dipole,
-//      energy, cell lists); then a second grid barrier.
+//   5. on accept: Alg. L.2 items (one contribution per half-warp on levels
+//      with <= 4 cells per axis, one updated cell per warp above) and one
+//      bookkeeping item (K, H, dipole, energy, cell lists); then a second
+//      grid barrier.
+// Displacements are formed as (offset of the point from its own cell centre)
+// minus (integer cell offset) x (cell width), which keeps FP64 work off the
+// items and keeps FP32 displacements accurate.
 // Template TE is the evaluation type: double (FP64 form) or float (FP32-eval
 // form: harmonics and near field in FP32; FP64 accumulators, energy, far
 // lattice operator, decision).
@@ -31,14 +38,29 @@ struct StepGeo {
   double q;
   double r[3], rn[3];
   int cf[3], cfn[3];
-  bool same;
   bool outside;  // free space: r' left the box
 };
+
+// Optional timers (RunParams.prof, 32 counters, globaltimer ns):
+//   [0..4] CTA 0 thread 0: own propose items, barrier-1 wait, decision,
+//          own accept items, barrier-2 wait; [5] steps, [6] accepted steps;
+//   [8+t] summed duration, [16+t] count, [24+t] max duration of items of
+//   type t: 0 E, 1 N, 2 F, 3 X, 4 small-level accept, 5 target accept,
+//   6 bookkeeping.
+__device__ __forceinline__ void prof_item(unsigned long long* prof, int type,
+                                          unsigned long long t0) {
+  const unsigned long long d = mc_globaltimer() - t0;
+  atomicAdd(&prof[8 + type], d);
+  atomicAdd(&prof[16 + type], 1ULL);
+  atomicMax(&prof[24 + type], d);
+}
 
 __device__ __forceinline__ bool is_square(int k) {
   int s = (int)sqrtf((float)k + 0.5f);
   return s * s == k;
 }
+
+constexpr double kInf = __builtin_huge_val();
 
 }  // namespace
 
@@ -49,11 +71,24 @@ __global__ void __launch_bounds__(MC_THREADS, 1)
   __shared__ HarmTabs<TE> tabs;
   __shared__ unsigned short il[8][189];
   __shared__ double stage[MC_WARPS][256];
-  __shared__ double s_dE, s_logu;
+  __shared__ double s_dE, s_logu, s_u;
+  __shared__ StepGeo sgeo;
+  // offset of r (side 0) / r' (side 1) from its cell centre on level l
+  __shared__ double s_off[2][MC_MAXLEV + 2][3];
+  // k * width of level l for k = -3..3 (k + 3), and in the evaluation type
+  __shared__ double s_kw[MC_MAXLEV + 2][7];
+  __shared__ TE s_kwe[MC_MAXLEV + 2][7];
 
   if (threadIdx.x == 0) S = *sysp;
   harm_tabs_init<TE>(&tabs);
   il_table_init(il);
+  __syncthreads();
+  for (int i = threadIdx.x; i < (MC_MAXLEV + 2) * 7; i += blockDim.x) {
+    const int l = i / 7, k = i % 7 - 3;
+    const double v = (l >= 1 && l <= S.L) ? k * S.lev_w[l] : 0.0;
+    s_kw[l][k + 3] = v;
+    s_kwe[l][k + 3] = (TE)v;
+  }
   __syncthreads();
 
   const int nCTA = gridDim.x, cta = blockIdx.x;
@@ -64,108 +99,139 @@ __global__ void __launch_bounds__(MC_THREADS, 1)
   const int nWarpsTot = nCTA * MC_WARPS;
   unsigned long long gen = 0;
   long long n_acc = 0, n_border = 0, steps_done = 0;
+  const bool prof_on = rp.prof != nullptr;
+  const bool prof_lead = prof_on && cta == 0 && threadIdx.x == 0;
+  unsigned long long tp0 = 0, tp1 = 0;
 
   for (long long t = 0; t < rp.nsteps; t++) {
     const int buf = (int)(t & 1);
+    if (prof_lead) tp0 = mc_globaltimer();
     // ------------------------------------------------------------ proposal
-    StepGeo g;
-    double u = 0.5;
-    if (rp.mode == 0) {
-      double d[3];
-      mc_proposal(rp.seed, (unsigned long long)(rp.step0 + t), 0u, S.n, rp.h, &g.j, d, &u);
-      const double4 pj = ldcg4(&S.ppos[g.j]);
-      g.r[0] = pj.x;
-      g.r[1] = pj.y;
-      g.r[2] = pj.z;
-      g.q = pj.w;
-      g.outside = false;
-#pragma unroll
-      for (int k = 0; k < 3; k++) {
-        double x = __dadd_rn(g.r[k], d[k]);
-        if (pbc) {
-          if (x < 0.0) x = __dadd_rn(x, S.a);
-          if (x >= S.a) x = __dsub_rn(x, S.a);
-        } else if (!(x >= 0.0 && x < S.a)) {
-          g.outside = true;
+    if (warp == 0) {
+      int j;
+      double q = 0.0, uu = 0.5, r = 0.0, rn = 0.0;
+      bool out = false;
+      if (rp.mode == 0) {
+        double d = 0.0;
+        mc_proposal_axis(rp.seed, (unsigned long long)(rp.step0 + t), 0u, S.n, rp.h,
+                         lane < 3 ? lane : 0, &j, &d, lane == 3 ? &uu : nullptr);
+        if (lane < 3) {
+          const double4 pj = ldcg4(&S.ppos[j]);
+          q = pj.w;
+          r = lane == 0 ? pj.x : (lane == 1 ? pj.y : pj.z);
+          double x = __dadd_rn(r, d);
+          if (pbc) {
+            if (x < 0.0) x = __dadd_rn(x, S.a);
+            if (x >= S.a) x = __dsub_rn(x, S.a);
+          } else if (!(x >= 0.0 && x < S.a)) {
+            out = true;
+          }
+          rn = x;
         }
-        g.rn[k] = x;
+      } else {
+        j = (int)rp.jg;
+        if (lane < 3) {
+          const double4 pj = ldcg4(&S.ppos[j]);
+          q = pj.w;
+          r = lane == 0 ? pj.x : (lane == 1 ? pj.y : pj.z);
+          rn = lane == 0 ? rp.rx : (lane == 1 ? rp.ry : rp.rz);
+        }
       }
-    } else {
-      g.j = (int)rp.jg;
-      const double4 pj = ldcg4(&S.ppos[g.j]);
-      g.r[0] = pj.x;
-      g.r[1] = pj.y;
-      g.r[2] = pj.z;
-      g.q = pj.w;
-      g.rn[0] = rp.rx;
-      g.rn[1] = rp.ry;
-      g.rn[2] = rp.rz;
-      g.outside = false;
-    }
-    const bool nomove = (g.r[0] == g.rn[0] && g.r[1] == g.rn[1] && g.r[2] == g.rn[2]);
+      const bool any_out = __any_sync(0xffffffffu, lane < 3 && out);
+      int cf = 0, cfn = 0;
+      if (lane < 3) {
+        cf = finest_coord(r, S.inv_wL, S.nL);
+        cfn = any_out ? cf : finest_coord(rn, S.inv_wL, S.nL);
+        sgeo.r[lane] = r;
+        sgeo.rn[lane] = rn;
+        sgeo.cf[lane] = cf;
+        sgeo.cfn[lane] = cfn;
+      }
+      // offsets from the cell centres: lane = side * 16 + level-slot, axis loop
+      {
+        const int side = lane >> 4, li = lane & 15;
+        const int l = L - li;
 #pragma unroll
-    for (int k = 0; k < 3; k++) {
-      g.cf[k] = finest_coord(g.r[k], S.inv_wL, S.nL);
-      g.cfn[k] = g.outside ? g.cf[k] : finest_coord(g.rn[k], S.inv_wL, S.nL);
+        for (int ax = 0; ax < 3; ax++) {
+          const double xo = __shfl_sync(0xffffffffu, r, ax), xn = __shfl_sync(0xffffffffu, rn, ax);
+          const int co = __shfl_sync(0xffffffffu, cf, ax), cnn = __shfl_sync(0xffffffffu, cfn, ax);
+          const double xs = side ? xn : xo;
+          const int cs = side ? cnn : co;
+          if (l >= 1 && l <= L && li <= L - 1) {
+            const int c = cs >> (L - l);
+            s_off[side][l][ax] = xs - ((double)c + 0.5) * S.lev_w[l];
+          }
+        }
+      }
+      if (lane == 0) {
+        sgeo.j = j;
+        sgeo.q = q;
+        sgeo.outside = any_out;
+      }
+      if (lane == 3) s_u = uu;
     }
-    g.same = (g.cf[0] == g.cfn[0] && g.cf[1] == g.cfn[1] && g.cf[2] == g.cfn[2]);
+    __syncthreads();
+    const StepGeo g = sgeo;
+    const double u = s_u;
+    const bool nomove = (g.r[0] == g.rn[0] && g.r[1] == g.rn[1] && g.r[2] == g.rn[2]);
+    const bool same = (g.cf[0] == g.cfn[0] && g.cf[1] == g.cfn[1] && g.cf[2] == g.cfn[2]);
 
     // -------------------------------------------------------- propose items
     const int nE = L - S.lmin + 1;
-    const int nN = g.same ? 27 : 54;
+    const int nN = same ? 27 : 54;
     const int nRB = (C + 31) / 32;
     const int nF = pbc ? nRB * MC_NF_COLS : 0;
-    const int nItems = nE + nN + nF + 1;
+    const int nItems = nE + nN + nF + 2;  // + X + U
     double* part = S.partials + buf * MC_MAX_ITEMS;
 
     for (int it = warp * nCTA + cta; it < nItems; it += nWarpsTot) {
+      const unsigned long long t_item = prof_on ? mc_globaltimer() : 0ULL;
       double partial = 0.0;
       if (nomove || g.outside) {
         // no work: dE is 0 (no move) or +inf (left a free-space box)
-        if (it == nItems - 1) {
-          if (g.outside) partial = __longlong_as_double(0x7ff0000000000000LL);
-          if (lane == 0 && rp.mode == 0) part[MC_MAX_ITEMS - 1] = log(u);
-        }
+        if (it == nItems - 2 && g.outside) partial = kInf;
+        if (it == nItems - 1 && lane == 0 && rp.mode == 0) part[MC_MAX_ITEMS - 1] = log(u);
       } else if (it < nE) {
         // ---- E: Eq. (2) at r (half 0) and r' (half 1) on level l
         const int l = L - it, sh = L - l;
         const int* cc = half ? g.cfn : g.cf;
-        const double* x = half ? g.rn : g.r;
         const int cx = cc[0] >> sh, cy = cc[1] >> sh, cz = cc[2] >> sh;
         const int nl = S.lev_n[l];
-        const double w = S.lev_w[l];
-        const double dx = x[0] - (cx + 0.5) * w, dy = x[1] - (cy + 0.5) * w,
-                     dz = x[2] - (cz + 0.5) * w;
         const double* Lb = S.Lhat + (size_t)(S.lev_off[l] + (cx * nl + cy) * nl + cz) * C;
         const int m = hm;
+        double Ld[MC_PMAX + 1], Lid[MC_PMAX + 1];
+#pragma unroll
+        for (int n = 0; n <= MC_PMAX; n++) {
+          const bool on = n <= p && m <= n;
+          const int k = rl_re(n, m);
+          Ld[n] = on ? __ldcg(&Lb[k]) : 0.0;
+          Lid[n] = (on && m) ? __ldcg(&Lb[k + 1]) : 0.0;
+        }
         TE Lr[MC_PMAX + 1], Li[MC_PMAX + 1];
 #pragma unroll
         for (int n = 0; n <= MC_PMAX; n++) {
-          Lr[n] = TE(0);
-          Li[n] = TE(0);
-          if (n <= p && m <= n) {
-            const int k = rl_re(n, m);
-            Lr[n] = (TE)__ldcg(&Lb[k]);
-            if (m) Li[n] = (TE)__ldcg(&Lb[k + 1]);
-          }
+          Lr[n] = from_double<TE>(Ld[n]);
+          Li[n] = from_double<TE>(Lid[n]);
         }
+        const TE dx = from_double<TE>(s_off[half][l][0]), dy = from_double<TE>(s_off[half][l][1]),
+                 dz = from_double<TE>(s_off[half][l][2]);
         TE acc = TE(0);
-        regular_columns<TE>(&tabs, p, m, (TE)dx, (TE)dy, (TE)dz, [&](int n, TE cr, TE ci) {
+        regular_columns<TE>(&tabs, p, m, dx, dy, dz, [&](int n, TE cr, TE ci) {
           if (n >= m) acc += Lr[n] * cr - Li[n] * ci;
         });
         if (m > p) acc = TE(0);
         if (m > 0) acc *= TE(2);
         acc = half_sum(acc);
-        const double psi = (double)acc;
-        const double psin = __shfl_sync(0xffffffffu, psi, 16);
-        partial = g.q * (psin - psi);
+        const TE accn = __shfl_sync(0xffffffffu, acc, 16);
+        partial = g.q * to_double(accn - acc);
       } else if (it < nE + nN) {
         // ---- N: Alg. 1 over one near cell (27 cells of the extended domain)
         const int k0 = it - nE;
-        const int k = g.same ? k0 : (k0 % 27);
-        const int side = g.same ? 2 : (k0 / 27);  // 0 old, 1 new, 2 both
+        const int k = same ? k0 : (k0 % 27);
+        const int side = same ? 2 : (k0 / 27);  // 0 old, 1 new, 2 both
         const int* cc = (side == 1) ? g.cfn : g.cf;
-        const int e0 = cc[0] + k / 9 - 1, e1 = cc[1] + (k / 3) % 3 - 1, e2 = cc[2] + k % 3 - 1;
+        const int d0 = k / 9 - 1, d1 = (k / 3) % 3 - 1, d2 = k % 3 - 1;
+        const int e0 = cc[0] + d0, e1 = cc[1] + d1, e2 = cc[2] + d2;
         const int nL = S.nL;
         bool valid = true;
         int c0, c1, c2, s0 = 0, s1 = 0, s2 = 0;
@@ -186,22 +252,24 @@ __global__ void __launch_bounds__(MC_THREADS, 1)
           const int cell = (c0 * nL + c1) * nL + c2;
           const int cnt = __ldcg(&S.ccount[cell]);
           const bool zero_shift = (s0 == 0 && s1 == 0 && s2 == 0);
-          const double sx = s0 * S.a, sy = s1 * S.a, sz = s2 * S.a;
           bool ovl = false;
           if (sizeof(TE) == 8) {
+            // query points moved by minus the image shift
+            const double sx = s0 * S.a, sy = s1 * S.a, sz = s2 * S.a;
+            const double ox = g.r[0] - sx, oy = g.r[1] - sy, oz = g.r[2] - sz;
+            const double nx = g.rn[0] - sx, ny = g.rn[1] - sy, nz = g.rn[2] - sz;
             double acc = 0.0;
             for (int s = lane; s < cnt; s += 32) {
               const double4 xi = ldcg4(&S.cpos[(size_t)cell * S.cap + s]);
-              const double xx = xi.x + sx, yy = xi.y + sy, zz = xi.z + sz;
               if (side != 1) {
                 const int pid = __ldcg(&S.cpid[(size_t)cell * S.cap + s]);
                 if (!(pid == g.j && zero_shift)) {
-                  const double ax = g.r[0] - xx, ay = g.r[1] - yy, az = g.r[2] - zz;
+                  const double ax = ox - xi.x, ay = oy - xi.y, az = oz - xi.z;
                   acc -= g.q * xi.w * rsqrt(ax * ax + ay * ay + az * az);
                 }
               }
               if (side != 0) {
-                const double bx = g.rn[0] - xx, by = g.rn[1] - yy, bz = g.rn[2] - zz;
+                const double bx = nx - xi.x, by = ny - xi.y, bz = nz - xi.z;
                 const double d2 = bx * bx + by * by + bz * bz;
                 if (d2 == 0.0) ovl = true;
                 acc += g.q * xi.w * rsqrt(d2);
@@ -209,16 +277,21 @@ __global__ void __launch_bounds__(MC_THREADS, 1)
             }
             partial = warp_sum(acc);
           } else {
-            // positions relative to the (image) cell centre, in FP32
-            const double w = S.lev_w[L];
-            const double Rx = (c0 + 0.5) * w + sx, Ry = (c1 + 0.5) * w + sy,
-                         Rz = (c2 + 0.5) * w + sz;
-            const float ox = (float)(g.r[0] - Rx), oy = (float)(g.r[1] - Ry),
-                        oz = (float)(g.r[2] - Rz);
-            const float nx = (float)(g.rn[0] - Rx), ny = (float)(g.rn[1] - Ry),
-                        nz = (float)(g.rn[2] - Rz);
+            // FP32: slot positions are stored relative to their cell centre;
+            // the query points relative to this (image) cell's centre follow
+            // from their finest-cell offsets and the integer cell offset
+            // old point: cell offset of the near cell relative to cf
+            const int oo0 = e0 - g.cf[0], oo1 = e1 - g.cf[1], oo2 = e2 - g.cf[2];
+            const int on0 = e0 - g.cfn[0], on1 = e1 - g.cfn[1], on2 = e2 - g.cfn[2];
+            const double wL = S.lev_w[L];
+            const float ox = d2f_int(s_off[0][L][0] - oo0 * wL),
+                        oy = d2f_int(s_off[0][L][1] - oo1 * wL),
+                        oz = d2f_int(s_off[0][L][2] - oo2 * wL);
+            const float nx = d2f_int(s_off[1][L][0] - on0 * wL),
+                        ny = d2f_int(s_off[1][L][1] - on1 * wL),
+                        nz = d2f_int(s_off[1][L][2] - on2 * wL);
             float acc = 0.0f;
-            const float qf = (float)g.q;
+            const float qf = d2f_int(g.q);
             for (int s = lane; s < cnt; s += 32) {
               const float4 xi = __ldcg(&S.cpos32[(size_t)cell * S.cap + s]);
               if (side != 1) {
@@ -235,9 +308,9 @@ __global__ void __launch_bounds__(MC_THREADS, 1)
                 acc += qf * xi.w * rsqrtf(d2);
               }
             }
-            partial = (double)warp_sum(acc);
+            partial = f2d_int(warp_sum(acc));
           }
-          if (__any_sync(0xffffffffu, ovl)) partial = __longlong_as_double(0x7ff0000000000000LL);
+          if (__any_sync(0xffffffffu, ovl)) partial = kInf;
         }
       } else if (it < nE + nN + nF) {
         // ---- F: far lattice, Sec. 3.3 (iv) in the factored form
@@ -248,15 +321,17 @@ __global__ void __launch_bounds__(MC_THREADS, 1)
         const double* x = half ? g.rn : g.r;
         const double c1 = 0.5 * S.a;
         double* st = stage[warp];
-        const TE dx = (TE)(x[0] - c1), dy = (TE)(x[1] - c1), dz = (TE)(x[2] - c1);
+        const TE qe = from_double<TE>(g.q);
+        const TE dx = from_double<TE>(x[0] - c1), dy = from_double<TE>(x[1] - c1),
+                 dz = from_double<TE>(x[2] - c1);
         regular_columns<TE>(&tabs, p, m, dx, dy, dz, [&](int n, TE cr, TE ci) {
           const TE nr = __shfl_xor_sync(0xffffffffu, cr, 16);
           const TE ni = __shfl_xor_sync(0xffffffffu, ci, 16);
           if (half == 0 && m <= p && n >= m) {
             // dK = q (conj Rt(r' - R1) - conj Rt(r - R1))
             const int k = rl_re(n, m);
-            st[k] = g.q * ((double)nr - (double)cr);
-            if (m) st[k + 1] = -g.q * ((double)ni - (double)ci);
+            st[k] = to_double(qe * (nr - cr));
+            if (m) st[k + 1] = to_double(-qe * (ni - ci));
           }
         });
         __syncwarp();
@@ -276,44 +351,59 @@ __global__ void __launch_bounds__(MC_THREADS, 1)
         }
         partial = warp_sum(contrib);
         __syncwarp();
-      } else {
-        // ---- X: periodic self-interaction correction (Sec. 3.3, last item),
-        //         dipole term (tinfoil reading), log(u)
-        double v = 0.0;
+      } else if (it == nItems - 2) {
+        // ---- X: periodic self-interaction correction (Sec. 3.3, last item)
+        //         and the dipole term (tinfoil reading)
+        const TE q2 = from_double<TE>(g.q * g.q);
+        const TE ddx = from_double<TE>(g.rn[0] - g.r[0]), ddy = from_double<TE>(g.rn[1] - g.r[1]),
+                 ddz = from_double<TE>(g.rn[2] - g.r[2]);
+        const TE ae = from_double<TE>(S.a);
+        TE v = TE(0);
         if (pbc) {
           if (lane < 27) {
-            const double ax = g.rn[0] - (g.r[0] + (lane / 9 - 1) * S.a);
-            const double ay = g.rn[1] - (g.r[1] + ((lane / 3) % 3 - 1) * S.a);
-            const double az = g.rn[2] - (g.r[2] + (lane % 3 - 1) * S.a);
-            v = -g.q * g.q * rsqrt(ax * ax + ay * ay + az * az);
+            const TE ax = ddx - TE(lane / 9 - 1) * ae;
+            const TE ay = ddy - TE((lane / 3) % 3 - 1) * ae;
+            const TE az = ddz - TE(lane % 3 - 1) * ae;
+            v = -q2 * mc_rsqrt(ax * ax + ay * ay + az * az);
           }
         } else if (lane == 0) {
-          const double ax = g.rn[0] - g.r[0], ay = g.rn[1] - g.r[1], az = g.rn[2] - g.r[2];
-          v = -g.q * g.q * rsqrt(ax * ax + ay * ay + az * az);
+          v = -q2 * mc_rsqrt(ddx * ddx + ddy * ddy + ddz * ddz);
         }
-        partial = warp_sum(v);
+        partial = to_double(warp_sum(v));
         if (pbc) {
           partial += g.q * g.q / S.a * kImageConst;
           if (S.dip == 0) {
             const double cdip = -2.0 * kPi / (3.0 * S.V);
             double D2 = 0.0, Dn2 = 0.0;
 #pragma unroll
-            for (int k = 0; k < 3; k++) {
-              const double D = __ldcg(&S.dipv[k]);
-              const double Dn = D + g.q * (g.rn[k] - g.r[k]);
+            for (int kk = 0; kk < 3; kk++) {
+              const double D = __ldcg(&S.dipv[kk]);
+              const double Dn = D + g.q * (g.rn[kk] - g.r[kk]);
               D2 += D * D;
               Dn2 += Dn * Dn;
             }
             partial += cdip * Dn2 - cdip * D2;
           }
         }
+      } else {
+        // ---- U: log(u) for the Metropolis test
         if (lane == 0 && rp.mode == 0) part[MC_MAX_ITEMS - 1] = log(u);
       }
       if (lane == 0) part[it] = partial;
+      if (prof_on && lane == 0)
+        prof_item(rp.prof, it < nE ? 0 : (it < nE + nN ? 1 : (it < nE + nN + nF ? 2 : 3)), t_item);
     }
 
+    if (prof_lead) {
+      tp1 = mc_globaltimer();
+      rp.prof[0] += tp1 - tp0;
+    }
     gen++;
     if (!grid_barrier(S.bar, gen * (unsigned long long)nCTA, S.status, rp.wait_ns)) break;
+    if (prof_lead) {
+      tp0 = mc_globaltimer();
+      rp.prof[1] += tp0 - tp1;
+    }
 
     // ------------------------------------------------ decision (every CTA)
     if (warp == 0) {
@@ -349,6 +439,11 @@ __global__ void __launch_bounds__(MC_THREADS, 1)
       }
     }
     steps_done++;
+    if (prof_lead) {
+      tp1 = mc_globaltimer();
+      rp.prof[2] += tp1 - tp0;
+      rp.prof[5] += 1;
+    }
     if (!accept || nomove) {
       if (accept) n_acc++;
       if (accept && cta == 0 && threadIdx.x == 0) S.energy[0] += dE_used;
@@ -358,96 +453,159 @@ __global__ void __launch_bounds__(MC_THREADS, 1)
     n_acc++;
 
     // --------------------------------------------------------- accept items
-    // level item counts: small levels (<= 4 cells per axis) enumerate every
-    // canonical cell, larger ones the interaction lists of alpha' (owners)
-    // and of alpha (owners unless also in IL(alpha')).
+    // level item counts: on small levels (<= 4 cells per axis) item k takes
+    // entry k of IL(alpha) (half 0) and of IL(alpha') (half 1), each its own
+    // contribution; on larger levels one item per updated target cell: the
+    // interaction list of alpha' (owners) and of alpha (owners unless the
+    // target is also in IL(alpha')).
     int lev_items[MC_MAXLEV + 2], lev_start[MC_MAXLEV + 2];
-    int nA = 1;  // item 0: bookkeeping
+    // item 0: bookkeeping; items 1..nKH: K and H += G dK, 32 entries each
+    const int nKH = pbc ? (C + 31) / 32 : 0;
+    int nA = 1 + nKH;
     for (int l = L; l >= S.lmin; l--) {
       const int sh = L - l, nl = S.lev_n[l];
       const bool samel = ((g.cf[0] >> sh) == (g.cfn[0] >> sh)) &&
                          ((g.cf[1] >> sh) == (g.cfn[1] >> sh)) &&
                          ((g.cf[2] >> sh) == (g.cfn[2] >> sh));
-      lev_items[l] = (nl <= 4) ? nl * nl * nl : (samel ? 189 : 378);
+      lev_items[l] = (nl <= 4) ? 189 : (samel ? 189 : 378);
       lev_start[l] = nA;
       nA += lev_items[l];
     }
     for (int it = warp * nCTA + cta; it < nA; it += nWarpsTot) {
+      const unsigned long long t_item = prof_on ? mc_globaltimer() : 0ULL;
       if (it == 0) {
         // ---- bookkeeping: K, H, dipole, energy, cell lists
-        if (pbc) {
-          for (int k = lane; k < C; k += 32) {
-            S.Khat[k] += __ldcg(&S.dK[(size_t)buf * C + k]);
-            double gs = 0.0;
-            for (int cb = 0; cb < MC_NF_COLS; cb++)
-              gs += __ldcg(&S.gK[(size_t)buf * MC_NF_COLS * C + (size_t)cb * C + k]);
-            S.Hhat[k] += gs;
-          }
-        }
-        if (lane == 0) {
-#pragma unroll
-          for (int k = 0; k < 3; k++) S.dipv[k] += g.q * (g.rn[k] - g.r[k]);
-          S.energy[0] += dE_used;
-          const int nL = S.nL, cap = S.cap;
-          const int co = (g.cf[0] * nL + g.cf[1]) * nL + g.cf[2];
-          const int cn = (g.cfn[0] * nL + g.cfn[1]) * nL + g.cfn[2];
-          const double w = S.lev_w[L];
-          const float4 rel = make_float4((float)(g.rn[0] - (g.cfn[0] + 0.5) * w),
-                                         (float)(g.rn[1] - (g.cfn[1] + 0.5) * w),
-                                         (float)(g.rn[2] - (g.cfn[2] + 0.5) * w), (float)g.q);
-          const double4 np = make_double4(g.rn[0], g.rn[1], g.rn[2], g.q);
-          const int so = S.pslot[g.j];
-          if (co == cn) {
-            S.cpos[so] = np;
-            S.cpos32[so] = rel;
-          } else {
-            const int last = S.ccount[co] - 1;
-            const int sl = co * cap + last;
-            if (so != sl) {
-              S.cpos[so] = S.cpos[sl];
-              S.cpos32[so] = S.cpos32[sl];
-              const int pid = S.cpid[sl];
+        const int nL = S.nL, cap = S.cap;
+        const int co = (g.cf[0] * nL + g.cf[1]) * nL + g.cf[2];
+        const int cn = (g.cfn[0] * nL + g.cfn[1]) * nL + g.cfn[2];
+        // the loads the move needs, issued together by lanes 0..2
+        int so = 0, cnt_o = 0, cnt_n = 0;
+        if (lane == 0) so = S.pslot[g.j];
+        if (lane == 1) cnt_o = S.ccount[co];
+        if (lane == 2) cnt_n = S.ccount[cn];
+        so = __shfl_sync(0xffffffffu, so, 0);
+        cnt_o = __shfl_sync(0xffffffffu, cnt_o, 1);
+        cnt_n = __shfl_sync(0xffffffffu, cnt_n, 2);
+        const double4 np = make_double4(g.rn[0], g.rn[1], g.rn[2], g.q);
+        const float4 rel = make_float4(d2f_int(s_off[1][L][0]), d2f_int(s_off[1][L][1]),
+                                       d2f_int(s_off[1][L][2]), d2f_int(g.q));
+        if (co == cn) {
+          if (lane == 0) S.cpos[so] = np;
+          if (lane == 1) S.cpos32[so] = rel;
+        } else {
+          const int last = cnt_o - 1;
+          const int sl = co * cap + last;
+          if (so != sl) {
+            // move the cell's last slot into the freed one
+            double4 v4 = make_double4(0, 0, 0, 0);
+            float4 f4 = make_float4(0, 0, 0, 0);
+            int pid = 0;
+            if (lane == 0) v4 = S.cpos[sl];
+            if (lane == 1) f4 = S.cpos32[sl];
+            if (lane == 2) pid = S.cpid[sl];
+            pid = __shfl_sync(0xffffffffu, pid, 2);
+            if (lane == 0) S.cpos[so] = v4;
+            if (lane == 1) S.cpos32[so] = f4;
+            if (lane == 2) {
               S.cpid[so] = pid;
               S.pslot[pid] = so;
             }
-            S.ccount[co] = last;
-            const int sn = S.ccount[cn];
-            if (sn >= cap) {
-              atomicExch(S.status, MCD_ERR_CAPACITY);
-            } else {
-              const int slot = cn * cap + sn;
-              S.cpos[slot] = np;
-              S.cpos32[slot] = rel;
-              S.cpid[slot] = g.j;
-              S.pslot[g.j] = slot;
-              S.ccount[cn] = sn + 1;
-            }
           }
-          S.ppos[g.j] = np;
+          if (lane == 3) S.ccount[co] = last;
+          if (cnt_n >= cap) {
+            if (lane == 0) atomicExch(S.status, MCD_ERR_CAPACITY);
+          } else {
+            const int slot = cn * cap + cnt_n;
+            if (lane == 0) S.cpos[slot] = np;
+            if (lane == 1) S.cpos32[slot] = rel;
+            if (lane == 2) S.cpid[slot] = g.j;
+            if (lane == 4) S.pslot[g.j] = slot;
+            if (lane == 5) S.ccount[cn] = cnt_n + 1;
+          }
         }
+        if (lane == 6) S.ppos[g.j] = np;
+        if (lane == 7) S.energy[0] += dE_used;
+        if (lane >= 8 && lane < 11) S.dipv[lane - 8] += g.q * (g.rn[lane - 8] - g.r[lane - 8]);
+        if (prof_on && lane == 0) prof_item(rp.prof, 6, t_item);
         continue;
       }
-      // ---- level target item (Alg. L.2)
+      if (it <= nKH) {
+        // ---- K += dK, H += G dK (sum of the column-block partials)
+        const int k = (it - 1) * 32 + lane;
+        if (k < C) {
+          double gv[MC_NF_COLS];
+#pragma unroll
+          for (int cb = 0; cb < MC_NF_COLS; cb++)
+            gv[cb] = __ldcg(&S.gK[(size_t)buf * MC_NF_COLS * C + (size_t)cb * C + k]);
+          const double dk = __ldcg(&S.dK[(size_t)buf * C + k]);
+          const double kh = __ldcg(&S.Khat[k]), hh = __ldcg(&S.Hhat[k]);
+          double gs = 0.0;
+#pragma unroll
+          for (int cb = 0; cb < MC_NF_COLS; cb++) gs += gv[cb];
+          __stcg(&S.Khat[k], kh + dk);
+          __stcg(&S.Hhat[k], hh + gs);
+        }
+        if (prof_on && lane == 0) prof_item(rp.prof, 6, t_item);
+        continue;
+      }
+      // ---- Alg. L.2 items
       int l = L;
       while (l > S.lmin && it >= lev_start[l] + lev_items[l]) l--;
       const int k = it - lev_start[l];
       const int sh = L - l, nl = S.lev_n[l];
-      const double w = S.lev_w[l];
       const int co[3] = {g.cf[0] >> sh, g.cf[1] >> sh, g.cf[2] >> sh};
       const int cn[3] = {g.cfn[0] >> sh, g.cfn[1] >> sh, g.cfn[2] >> sh};
+      const int m = hm;
+      if (nl <= 4) {
+        // entry k of this half's interaction list; image copies make targets
+        // repeat across entries, so the update goes through L2 atomic adds
+        const int* cs = half ? cn : co;
+        const int par = ((cs[0] & 1) << 2) | ((cs[1] & 1) << 1) | (cs[2] & 1);
+        int ox, oy, oz;
+        il_unpack(il[par][k], &ox, &oy, &oz);
+        const int e[3] = {cs[0] + ox, cs[1] + oy, cs[2] + oz};
+        const bool valid = pbc || (e[0] >= 0 && e[0] < nl && e[1] >= 0 && e[1] < nl &&
+                                   e[2] >= 0 && e[2] < nl);
+        const int t3[3] = {mc_wrap_coord(e[0], nl), mc_wrap_coord(e[1], nl),
+                           mc_wrap_coord(e[2], nl)};
+        const TE f = valid ? from_double<TE>(half ? g.q : -g.q) : TE(0);
+        TE dx = TE(3), dy = TE(3), dz = TE(3);
+        if (valid) {
+          if (sizeof(TE) == 8) {
+            dx = (TE)(s_off[half][l][0] - s_kw[l][ox + 3]);
+            dy = (TE)(s_off[half][l][1] - s_kw[l][oy + 3]);
+            dz = (TE)(s_off[half][l][2] - s_kw[l][oz + 3]);
+          } else {
+            dx = from_double<TE>(s_off[half][l][0]) - s_kwe[l][ox + 3];
+            dy = from_double<TE>(s_off[half][l][1]) - s_kwe[l][oy + 3];
+            dz = from_double<TE>(s_off[half][l][2]) - s_kwe[l][oz + 3];
+          }
+        }
+        double* Lt = S.Lhat + (size_t)(S.lev_off[l] + (t3[0] * nl + t3[1]) * nl + t3[2]) * C;
+        irregular_columns<TE>(&tabs, p, m, dx, dy, dz, [&](int n, TE cr, TE ci) {
+          if (valid && m <= p && n >= m) {
+            const int kk = rl_re(n, m);
+            atomicAdd(&Lt[kk], to_double(f * cr));
+            if (m) atomicAdd(&Lt[kk + 1], to_double(-f * ci));
+          }
+        });
+        if (prof_on && lane == 0) prof_item(rp.prof, 4, t_item);
+        continue;
+      }
       int tc[3];
       bool owner = true;
-      if (nl <= 4) {
-        tc[0] = k / (nl * nl);
-        tc[1] = (k / nl) % nl;
-        tc[2] = k % nl;
-      } else {
-        const bool from_new = (lev_items[l] == 189) || (k < 189);
+      const bool samel = lev_items[l] == 189;
+      const bool from_new = samel || (k < 189);
+      int o_known[3];
+      {
         const int kk = (k < 189) ? k : k - 189;
         const int* base = from_new ? cn : co;
         const int par = ((base[0] & 1) << 2) | ((base[1] & 1) << 1) | (base[2] & 1);
         int ox, oy, oz;
         il_unpack(il[par][kk], &ox, &oy, &oz);
+        o_known[0] = ox;
+        o_known[1] = oy;
+        o_known[2] = oz;
         const int e[3] = {base[0] + ox, base[1] + oy, base[2] + oz};
         if (!pbc && (e[0] < 0 || e[0] >= nl || e[1] < 0 || e[1] >= nl || e[2] < 0 || e[2] >= nl))
           owner = false;
@@ -464,67 +622,89 @@ __global__ void __launch_bounds__(MC_THREADS, 1)
         }
       }
       if (!owner) continue;
-      // contributions of this half's side: bit s of mask = image shift s
+      // this half's contribution: the (at most one, nl >= 8) image of the
+      // target inside the half's interaction list.  The offset is known for
+      // the list the item came from (and for both halves when alpha =
+      // alpha' on this level); only the other half of a mixed item searches.
       const int* cs = half ? cn : co;
-      unsigned mask = 0u;
-      for (int s = 0; s < 27; s++) {
-        const int sx = s / 9 - 1, sy = (s / 3) % 3 - 1, sz = s % 3 - 1;
-        if (!pbc && (sx || sy || sz)) continue;
-        if (in_il(tc[0] + sx * nl - cs[0], tc[1] + sy * nl - cs[1], tc[2] + sz * nl - cs[2], cs[0],
-                  cs[1], cs[2]))
-          mask |= 1u << s;
-      }
-      const int cnt = __popc(mask);
-      const int cnt_o = __shfl_xor_sync(0xffffffffu, cnt, 16);
-      const int iters = max(cnt, cnt_o);
-      if (iters == 0) continue;
-      const double* x = half ? g.rn : g.r;
-      const TE sg = (TE)(half ? g.q : -g.q);
-      const int m = hm;
-      TE ar[MC_PMAX + 1], ai[MC_PMAX + 1];
-#pragma unroll
-      for (int n = 0; n <= MC_PMAX; n++) {
-        ar[n] = TE(0);
-        ai[n] = TE(0);
-      }
-      for (int i = 0; i < iters; i++) {
-        const bool act = i < cnt;
-        int s = 0;
-        if (act) {
-          unsigned mm = mask;
-          for (int b = 0; b < i; b++) mm &= mm - 1u;
-          s = __ffs(mm) - 1;
+      int ofs[3] = {o_known[0], o_known[1], o_known[2]};
+      bool have;
+      if (samel || (from_new && half == 1) || (!from_new && half == 0)) {
+        have = true;
+      } else if (!from_new) {
+        have = false;  // the target is not in IL(alpha') (else not owner)
+      } else {
+        have = false;
+        for (int s = 0; s < 27 && !have; s++) {
+          const int sx = s / 9 - 1, sy = (s / 3) % 3 - 1, sz = s % 3 - 1;
+          if (!pbc && (sx || sy || sz)) continue;
+          const int o0 = tc[0] + sx * nl - cs[0], o1 = tc[1] + sy * nl - cs[1],
+                    o2 = tc[2] + sz * nl - cs[2];
+          if (in_il(o0, o1, o2, cs[0], cs[1], cs[2])) {
+            have = true;
+            ofs[0] = o0;
+            ofs[1] = o1;
+            ofs[2] = o2;
+          }
         }
-        const int sx = s / 9 - 1, sy = (s / 3) % 3 - 1, sz = s % 3 - 1;
-        const double Rx = (tc[0] + sx * nl + 0.5) * w, Ry = (tc[1] + sy * nl + 0.5) * w,
-                     Rz = (tc[2] + sz * nl + 0.5) * w;
-        // inactive lanes evaluate a harmless point (never consumed)
-        const TE dx = act ? (TE)(x[0] - Rx) : TE(3), dy = act ? (TE)(x[1] - Ry) : TE(3),
-                 dz = act ? (TE)(x[2] - Rz) : TE(3);
-        const TE f = act ? sg : TE(0);
-        irregular_columns<TE>(&tabs, p, m, dx, dy, dz, [&](int n, TE cr, TE ci) {
-          ar[n] += f * cr;
-          ai[n] -= f * ci;
-        });
       }
+      const TE f = have ? from_double<TE>(half ? g.q : -g.q) : TE(0);
+      TE dx = TE(3), dy = TE(3), dz = TE(3);
+      if (have) {
+        if (sizeof(TE) == 8) {
+          dx = (TE)(s_off[half][l][0] - s_kw[l][ofs[0] + 3]);
+          dy = (TE)(s_off[half][l][1] - s_kw[l][ofs[1] + 3]);
+          dz = (TE)(s_off[half][l][2] - s_kw[l][ofs[2] + 3]);
+        } else {
+          dx = from_double<TE>(s_off[half][l][0]) - s_kwe[l][ofs[0] + 3];
+          dy = from_double<TE>(s_off[half][l][1]) - s_kwe[l][ofs[1] + 3];
+          dz = from_double<TE>(s_off[half][l][2]) - s_kwe[l][ofs[2] + 3];
+        }
+      }
+      TE ar[MC_PMAX + 1], ai[MC_PMAX + 1];
+      irregular_columns<TE>(&tabs, p, m, dx, dy, dz, [&](int n, TE cr, TE ci) {
+        ar[n] = f * cr;
+        ai[n] = -f * ci;
+      });
       double* st = stage[warp];
 #pragma unroll
       for (int n = 0; n <= MC_PMAX; n++) {
-        const TE orr = __shfl_xor_sync(0xffffffffu, ar[n], 16);
-        const TE oii = __shfl_xor_sync(0xffffffffu, ai[n], 16);
-        if (half == 0 && n <= p && m <= n) {
-          const int kk = rl_re(n, m);
-          st[kk] = (double)ar[n] + (double)orr;
-          if (m) st[kk + 1] = (double)ai[n] + (double)oii;
+        if (n <= p) {
+          const TE orr = __shfl_xor_sync(0xffffffffu, ar[n], 16);
+          const TE oii = __shfl_xor_sync(0xffffffffu, ai[n], 16);
+          if (half == 0 && m <= n) {
+            const int kk = rl_re(n, m);
+            st[kk] = to_double(ar[n] + orr);
+            if (m) st[kk + 1] = to_double(ai[n] + oii);
+          }
         }
       }
       __syncwarp();
       double* Lt = S.Lhat + (size_t)(S.lev_off[l] + (tc[0] * nl + tc[1]) * nl + tc[2]) * C;
-      for (int kk = lane; kk < C; kk += 32) __stcg(&Lt[kk], __ldcg(&Lt[kk]) + st[kk]);
+      {
+        double v[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+          const int kk = lane + 32 * i;
+          v[i] = kk < C ? __ldcg(&Lt[kk]) : 0.0;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+          const int kk = lane + 32 * i;
+          if (kk < C) __stcg(&Lt[kk], v[i] + st[kk]);
+        }
+      }
       __syncwarp();
+      if (prof_on && lane == 0) prof_item(rp.prof, 5, t_item);
+    }
+    if (prof_lead) {
+      tp0 = mc_globaltimer();
+      rp.prof[3] += tp0 - tp1;
+      rp.prof[6] += 1;
     }
     gen++;
     if (!grid_barrier(S.bar, gen * (unsigned long long)nCTA, S.status, rp.wait_ns)) break;
+    if (prof_lead) rp.prof[4] += mc_globaltimer() - tp0;
     if (rp.stop_after_accepts > 0 && n_acc >= rp.stop_after_accepts) break;
   }
   if (cta == 0 && threadIdx.x == 0) {

@@ -29,7 +29,7 @@
 #define MC_WARPS (MC_THREADS / 32)
 #define MC_MAX_ITEMS 256
 #define MC_NF_ROWS 6    // far-field row blocks of 32 rows (covers C <= 192)
-#define MC_NF_COLS 8    // far-field column chunks
+#define MC_NF_COLS 16   // far-field column chunks
 
 // ---------------------------------------------------------------- state
 struct McSys {
@@ -74,6 +74,7 @@ struct RunParams {
   double* log_dE;
   unsigned char* log_acc;
   long long wait_ns;
+  unsigned long long* prof;  // optional phase/item timers (see mc_chain.cu), may be null
 };
 
 // ------------------------------------------------------------ error codes
@@ -120,6 +121,51 @@ __device__ __forceinline__ void mc_proposal(unsigned long long seed, unsigned lo
   *u = __dmul_rn(__dadd_rn(__dmul_rn((double)(B[0] >> 5), 67108864.0), (double)(B[1] >> 6)),
                  1.1102230246251565e-16);
 }
+
+// One axis of the proposal: every lane runs both Philox blocks (integer
+// work), the FP64 arithmetic of the displacement is per axis, u only where
+// requested.
+__device__ __forceinline__ void mc_proposal_axis(unsigned long long seed, unsigned long long s,
+                                                 uint32_t chain, int n, double h, int axis, int* j,
+                                                 double* d, double* u) {
+  uint32_t A[4] = {(uint32_t)s, (uint32_t)(s >> 32), chain, 0u};
+  uint32_t B[4] = {(uint32_t)s, (uint32_t)(s >> 32), chain, 1u};
+  philox4x32_10(A, (uint32_t)seed, (uint32_t)(seed >> 32));
+  philox4x32_10(B, (uint32_t)seed, (uint32_t)(seed >> 32));
+  *j = (int)(((unsigned long long)A[0] * (unsigned long long)n) >> 32);
+  const uint32_t w = axis == 0 ? A[1] : (axis == 1 ? A[2] : A[3]);
+  const double uk = __dmul_rn(__dadd_rn((double)w, 0.5), 2.3283064365386963e-10);
+  *d = __dmul_rn(h, __dsub_rn(__dmul_rn(2.0, uk), 1.0));
+  if (u)
+    *u = __dmul_rn(__dadd_rn(__dmul_rn((double)(B[0] >> 5), 67108864.0), (double)(B[1] >> 6)),
+                   1.1102230246251565e-16);
+}
+
+// IEEE-754 conversions on the integer pipe (the FP64 pipe is 1/64 rate).
+// float -> double is exact for normal floats; subnormal floats become 0.
+__device__ __forceinline__ double f2d_int(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e = (b >> 23) & 0xffu;
+  const uint32_t sign = b & 0x80000000u;
+  const uint32_t hi = e ? (sign | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3)) : sign;
+  const uint32_t lo = e ? (b << 29) : 0u;
+  return __hiloint2double((int)hi, (int)lo);
+}
+// double -> float rounded toward zero; |x| beyond the float range saturates
+// to +-inf, below it flushes to 0 (branch-free).
+__device__ __forceinline__ float d2f_int(double x) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const int e = (int)((hi >> 20) & 0x7ffu) - 896;
+  uint32_t mag = ((uint32_t)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  mag = (e <= 0) ? 0u : mag;
+  mag = (e >= 255) ? 0x7f800000u : mag;
+  return __uint_as_float((hi & 0x80000000u) | mag);
+}
+template <typename T> __device__ __forceinline__ T from_double(double x);
+template <> __device__ __forceinline__ double from_double<double>(double x) { return x; }
+template <> __device__ __forceinline__ float from_double<float>(double x) { return d2f_int(x); }
+__device__ __forceinline__ double to_double(double x) { return x; }
+__device__ __forceinline__ double to_double(float x) { return f2d_int(x); }
 
 // ---------------------------------------------------------- grid barrier
 // Monotone 64-bit arrival counter; thread 0 of every CTA arrives with a

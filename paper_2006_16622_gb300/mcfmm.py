@@ -22,7 +22,8 @@ SETUP_P2L = 0
 
 EXPORTED = ["mc_init", "mc_setup", "mc_propose", "mc_accept", "mc_run", "mc_energy",
             "mc_energy_fresh", "mc_get_positions", "mc_get_local", "mc_get_far",
-            "mc_lattice_sums", "mc_status", "mc_set_wait_limit", "mc_destroy", "mc_strerror"]
+            "mc_lattice_sums", "mc_status", "mc_set_wait_limit", "mc_profile", "mc_profile_read",
+            "mc_destroy", "mc_strerror"]
 
 
 class McStats(ctypes.Structure):
@@ -62,6 +63,8 @@ def load(path: str = LIB_PATH):
     L.mc_lattice_sums.argtypes = [I, P]
     L.mc_status.argtypes = [P]
     L.mc_set_wait_limit.argtypes = [P, I64]
+    L.mc_profile.argtypes = [P, I]
+    L.mc_profile_read.argtypes = [P, P]
     L.mc_destroy.argtypes = [P]
     L.mc_destroy.restype = None
     L.mc_strerror.argtypes = [I]
@@ -179,6 +182,14 @@ class Context:
 
     def status(self):
         return load().mc_status(self._h)
+
+    def profile(self, on=True):
+        _check(load().mc_profile(self._h, 1 if on else 0), "mc_profile")
+
+    def profile_read(self):
+        out = np.zeros(32, dtype=np.uint64)
+        _check(load().mc_profile_read(self._h, _ptr(out)), "mc_profile_read")
+        return out
 
     def set_wait_limit(self, ns):
         _check(load().mc_set_wait_limit(self._h, int(ns)), "mc_set_wait_limit")
