@@ -39,6 +39,7 @@ extern "C" {
 #define MC_ERR_ORDER (-9)      /* expansion order p outside 0..15 */
 #define MC_ERR_STATE (-10)     /* call out of order (e.g. propose before setup) */
 #define MC_ERR_NOMEM (-11)     /* device allocation failed */
+#define MC_ERR_SCRATCH (-12)   /* request larger than the fixed no-allocation scratch */
 
 #define MC_BC_PBC 0   /* periodic cube (paper Sec. 3.3) */
 #define MC_BC_FREE 1  /* free space (paper Sec. 3.3, first paragraph) */
@@ -135,6 +136,40 @@ int mc_profile(mc_ctx *ctx, int on);
 int mc_profile_read(mc_ctx *ctx, uint64_t *out);
 void mc_destroy(mc_ctx *ctx);
 const char *mc_strerror(int status);
+
+/* Size of the fixed device scratch of mc_p2l_level_noalloc, in doubles
+ * (8 MiB), held by every GPU that loads the library until the process exits. */
+#define MC_NOALLOC_SCRATCH_DOUBLES (1 << 20)
+
+/* Local expansions of one level, computed without any allocation.
+ *
+ * The paper has no counterpart: this is a service for callers that cannot
+ * let a library call cudaMalloc or cudaFree -- code that hands out every
+ * byte of device memory from its own pool, code running where an allocation
+ * would synchronise the device or is forbidden, embedders that audit hidden
+ * allocations.  It computes the same coefficients as mc_setup + mc_get_local
+ * for one level (the gather form of Alg. L.3), from buffers the caller owns:
+ *   d_part        device, n rows of (x, y, z, q) doubles, grouped by finest
+ *                 cell (levels L: 2^(L-1) cells per axis, cell of a point =
+ *                 floor(x 2^(L-1) / box) clamped, linear index (i n + j) n + k);
+ *   d_cell_start  device, 8^(L-1) + 1 ints: the charges of finest cell c are
+ *                 rows [d_cell_start[c], d_cell_start[c+1]) of d_part;
+ *   n, box, levels, p, bc  as for mc_init; 2 <= level <= levels;
+ *   d_out         device, 8^(level-1) * (p+1)^2 doubles, written in the real
+ *                 layout and paper normalisation of mc_get_local;
+ *   cuda_stream   stream to launch on (NULL = legacy stream); the call only
+ *                 enqueues work and returns.
+ * Intermediate sums live in one file-scope device array of
+ * MC_NOALLOC_SCRATCH_DOUBLES doubles.  A level whose 8^(level-1) (p+1)^2
+ * coefficients exceed it is refused with MC_ERR_SCRATCH before any launch.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the one array: each call
+ * writes every scratch value it reads before reading it, so nothing needs
+ * clearing, but calls whose work overlaps on the GPU (other streams, other
+ * host threads) race on it and must be serialised by the caller. */
+int mc_p2l_level_noalloc(const double *d_part, const int *d_cell_start, int64_t n, double box,
+                         int levels, int level, int p, int bc, double *d_out, void *cuda_stream);
 
 #ifdef __cplusplus
 }

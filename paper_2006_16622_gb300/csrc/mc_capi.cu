@@ -178,6 +178,7 @@ const char* mc_strerror(int s) {
     case MC_ERR_ORDER: return "expansion order must be in 0..15";
     case MC_ERR_STATE: return "call out of order";
     case MC_ERR_NOMEM: return "device allocation failed";
+    case MC_ERR_SCRATCH: return "request exceeds the fixed no-allocation scratch";
     default: return "unknown status";
   }
 }

@@ -23,7 +23,7 @@ SETUP_P2L = 0
 EXPORTED = ["mc_init", "mc_setup", "mc_propose", "mc_accept", "mc_run", "mc_energy",
             "mc_energy_fresh", "mc_get_positions", "mc_get_local", "mc_get_far",
             "mc_lattice_sums", "mc_status", "mc_set_wait_limit", "mc_profile", "mc_profile_read",
-            "mc_destroy", "mc_strerror"]
+            "mc_destroy", "mc_strerror", "mc_p2l_level_noalloc"]
 
 
 class McStats(ctypes.Structure):
@@ -65,6 +65,7 @@ def load(path: str = LIB_PATH):
     L.mc_set_wait_limit.argtypes = [P, I64]
     L.mc_profile.argtypes = [P, I]
     L.mc_profile_read.argtypes = [P, P]
+    L.mc_p2l_level_noalloc.argtypes = [P, P, I64, D, I, I, I, I, P, P]
     L.mc_destroy.argtypes = [P]
     L.mc_destroy.restype = None
     L.mc_strerror.argtypes = [I]
@@ -90,6 +91,15 @@ def _ptr(a):
 def _check(code, what):
     if code != MC_OK:
         raise McError(code, what)
+
+
+def p2l_level_noalloc(d_part, d_cell_start, n, box, levels, level, p, bc, d_out, stream=None):
+    """Allocation-free level expansions from caller-owned device buffers
+    (raw device addresses as ints); see mc_p2l_level_noalloc in mcfmm.h."""
+    return load().mc_p2l_level_noalloc(ctypes.c_void_p(d_part), ctypes.c_void_p(d_cell_start),
+                                       int(n), float(box), int(levels), int(level), int(p),
+                                       int(bc), ctypes.c_void_p(d_out),
+                                       ctypes.c_void_p(stream) if stream else None)
 
 
 def lattice_sums(lmax: int):
