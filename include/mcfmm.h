@@ -137,6 +137,35 @@ int mc_profile_read(mc_ctx *ctx, uint64_t *out);
 void mc_destroy(mc_ctx *ctx);
 const char *mc_strerror(int status);
 
+/* ---- batched form: many independent chains in one persistent launch ----
+ * The contexts (created and set up with mc_init/mc_setup on the same device
+ * and with the same precision) keep ownership of their systems; a batch runs
+ * their chains concurrently, each on its own group of CTAs with its own grid
+ * barrier, in one cooperative launch replayed from a CUDA graph. */
+typedef struct mc_batch mc_batch;
+/* ctxs: n_chains context pointers (the batch does not own them; destroy the
+ * batch before its contexts).  The initial CTA split gives every chain at
+ * least one CTA, the rest in proportion to its number of levels. */
+int mc_batch_create(mc_batch **out, int n_chains, mc_ctx *const *ctxs);
+/* Autotuner: times short runs (trial_steps proposals per chain, which
+ * advance the chains) at one and two CTAs per chain, fits each chain's time
+ * per proposal t(g) = a + b/g, assigns the SMs greedily to minimise the
+ * slowest chain's time, then picks the far-field tile count (column blocks
+ * per row block, 1..16) with the shortest slowest-chain time. */
+int mc_batch_tune(mc_batch *b, int64_t trial_steps, double beta, double half_width);
+/* Runs n_steps proposals on every chain (seeds[i] keys chain i, Philox
+ * counter word 2 = i; step counters continue across calls).  The launch is
+ * captured once per (n_steps, beta, h, split, tiles) into a CUDA graph and
+ * replayed.  stats: n_chains entries or NULL (NULL and no logs = enqueue
+ * only).  Logs: host arrays of n_chains * n_steps entries or NULL (logged
+ * runs are not graphed). */
+int mc_batch_run(mc_batch *b, int64_t n_steps, const uint64_t *seeds, double beta,
+                 double half_width, mc_stats *stats, int64_t *log_j, double *log_dE,
+                 uint8_t *log_acc);
+/* CTAs given to each chain (n_chains ints) and the far-field tile count. */
+int mc_batch_info(mc_batch *b, int *ctas_out, int *nf_cols_out);
+void mc_batch_destroy(mc_batch *b);
+
 /* Size of the fixed device scratch of mc_p2l_level_noalloc, in doubles
  * (8 MiB), held by every GPU that loads the library until the process exits. */
 #define MC_NOALLOC_SCRATCH_DOUBLES (1 << 20)

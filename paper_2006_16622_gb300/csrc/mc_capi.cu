@@ -16,6 +16,9 @@
 // kernels defined in the other translation units
 cudaError_t mc_launch_chain(const McSys* d_sys, const RunParams& rp, int prec, int nCTA,
                             cudaStream_t stream);
+cudaError_t mc_launch_batch(const McSys* const* d_systems, RunParams* d_rps, const int* d_cta_chain,
+                            const int* d_cta_rank, const int* d_chain_ctas, int prec, int nCTA,
+                            cudaStream_t stream);
 int mc_chain_max_ctas(int prec);
 __global__ void k_cell_count(int, const double4*, double, int, int*, int*);
 __global__ void k_cell_fill(int, const int*, int, int*, int*);
@@ -111,6 +114,8 @@ int sync_status(mc_ctx* c) {
 int launch_chain(mc_ctx* c, RunParams& rp) {
   rp.wait_ns = c->wait_ns;
   rp.prof = c->d_prof;
+  rp.nf_cols = MC_NF_COLS;
+  rp.chain = 0u;
   CK(cudaMemsetAsync(c->h.bar, 0, sizeof(unsigned long long), c->stream));
   CK(cudaMemsetAsync(c->h.status, 0, sizeof(int), c->stream));
   CK(mc_launch_chain(c->d_sys, rp, c->h.prec, c->nCTA, c->stream));
@@ -622,6 +627,384 @@ int mc_status(mc_ctx* c) {
 int mc_set_wait_limit(mc_ctx* c, int64_t ns) {
   if (!c || ns < 0) return MC_ERR_ARG;
   c->wait_ns = ns;
+  return MC_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batches
+struct mc_batch {
+  int n;
+  std::vector<mc_ctx*> ctxs;
+  int prec, dev, sms;
+  cudaStream_t stream;
+  std::vector<int> ctas;  // CTAs per chain
+  int nf_cols;
+  // device copies
+  const McSys** d_systems;
+  RunParams* d_rps;
+  int *d_cta_chain, *d_cta_rank, *d_chain_ctas;
+  int nCTA;
+  // graph cache
+  cudaGraphExec_t gexec;
+  long long g_steps;
+  double g_beta, g_h;
+  int g_valid;
+  std::vector<uint64_t> seeds;
+  int seeds_valid;
+};
+
+namespace {
+
+int batch_upload_map(mc_batch* b) {
+  std::vector<int> cchain, crank;
+  for (int i = 0; i < b->n; i++)
+    for (int r = 0; r < b->ctas[i]; r++) {
+      cchain.push_back(i);
+      crank.push_back(r);
+    }
+  b->nCTA = (int)cchain.size();
+  if (b->nCTA > b->sms) return MC_ERR_ARG;
+  CK(cudaMemcpy(b->d_cta_chain, cchain.data(), sizeof(int) * b->nCTA, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(b->d_cta_rank, crank.data(), sizeof(int) * b->nCTA, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(b->d_chain_ctas, b->ctas.data(), sizeof(int) * b->n, cudaMemcpyHostToDevice));
+  if (b->g_valid) {
+    cudaGraphExecDestroy(b->gexec);
+    b->g_valid = 0;
+  }
+  return MC_OK;
+}
+
+// split `total` CTAs: one each, the rest by largest remainder of the weights
+std::vector<int> split_by_weight(const std::vector<double>& w, int total) {
+  const int n = (int)w.size();
+  std::vector<int> out(n, 1);
+  int left = total - n;
+  double sw = 0.0;
+  for (double x : w) sw += x;
+  if (left <= 0 || sw <= 0.0) return out;
+  std::vector<std::pair<double, int>> rem;
+  int used = 0;
+  for (int i = 0; i < n; i++) {
+    const double share = w[i] / sw * left;
+    const int fl = (int)floor(share);
+    out[i] += fl;
+    used += fl;
+    rem.push_back({share - fl, i});
+  }
+  std::sort(rem.begin(), rem.end(), [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
+    return x.first > y.first || (x.first == y.first && x.second < y.second);
+  });
+  for (int k = 0; k < left - used && k < n; k++) out[rem[k].second]++;
+  return out;
+}
+
+int batch_set_params(mc_batch* b, long long n_steps, const uint64_t* seeds, double beta, double h,
+                     long long* const* logj, double* const* logd, unsigned char* const* loga) {
+  std::vector<RunParams> rps(b->n);
+  // current step counters live on the device (advanced by the kernel)
+  std::vector<RunParams> cur(b->n);
+  CK(cudaMemcpy(cur.data(), b->d_rps, sizeof(RunParams) * b->n, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < b->n; i++) {
+    RunParams& rp = rps[i];
+    memset(&rp, 0, sizeof(rp));
+    rp.mode = 0;
+    rp.step0 = cur[i].step0;
+    rp.nsteps = n_steps;
+    rp.seed = seeds[i];
+    rp.beta = beta;
+    rp.h = h;
+    rp.wait_ns = b->ctxs[i]->wait_ns;
+    rp.nf_cols = b->nf_cols;
+    rp.chain = (unsigned)i;
+    if (logj) {
+      rp.log_j = logj[i];
+      rp.log_dE = logd[i];
+      rp.log_acc = loga[i];
+    }
+  }
+  CK(cudaMemcpy(b->d_rps, rps.data(), sizeof(RunParams) * b->n, cudaMemcpyHostToDevice));
+  return MC_OK;
+}
+
+int batch_enqueue(mc_batch* b) {
+  for (int i = 0; i < b->n; i++) {
+    CK(cudaMemsetAsync(b->ctxs[i]->h.bar, 0, sizeof(unsigned long long), b->stream));
+    CK(cudaMemsetAsync(b->ctxs[i]->h.status, 0, sizeof(int), b->stream));
+  }
+  CK(mc_launch_batch(b->d_systems, b->d_rps, b->d_cta_chain, b->d_cta_rank, b->d_chain_ctas,
+                     b->prec, b->nCTA, b->stream));
+  return MC_OK;
+}
+
+int batch_collect(mc_batch* b, mc_stats* stats, std::vector<long long>* ns) {
+  CK(cudaStreamSynchronize(b->stream));
+  int worst = MC_OK;
+  for (int i = 0; i < b->n; i++) {
+    int st = 0;
+    long long hs[4];
+    CK(cudaMemcpy(&st, b->ctxs[i]->h.status, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(hs, b->ctxs[i]->h.stats, sizeof(hs), cudaMemcpyDeviceToHost));
+    if (st != MC_OK) worst = st;
+    b->ctxs[i]->steps_total += hs[0];
+    if (stats) {
+      memset(&stats[i], 0, sizeof(mc_stats));
+      stats[i].steps = hs[0];
+      stats[i].accepted = hs[1];
+      stats[i].borderline = hs[2];
+      CK(cudaMemcpy(&stats[i].energy, b->ctxs[i]->h.energy, sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    if (ns) (*ns)[i] = hs[3];
+  }
+  return worst;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mc_batch_create(mc_batch** out, int n_chains, mc_ctx* const* ctxs) {
+  if (!out || n_chains < 1 || !ctxs) return MC_ERR_ARG;
+  *out = nullptr;
+  for (int i = 0; i < n_chains; i++) {
+    if (!ctxs[i]) return MC_ERR_ARG;
+    if (!ctxs[i]->setup_done) return MC_ERR_STATE;
+    if (ctxs[i]->h.prec != ctxs[0]->h.prec || ctxs[i]->dev != ctxs[0]->dev) return MC_ERR_ARG;
+    for (int k = 0; k < i; k++)
+      if (ctxs[k] == ctxs[i]) return MC_ERR_ARG;
+  }
+  mc_batch* b = new mc_batch();
+  b->n = n_chains;
+  b->ctxs.assign(ctxs, ctxs + n_chains);
+  b->prec = ctxs[0]->h.prec;
+  b->dev = ctxs[0]->dev;
+  b->stream = ctxs[0]->stream;
+  if (cudaSetDevice(b->dev) != cudaSuccess) {
+    delete b;
+    return MC_ERR_CUDA;
+  }
+  b->sms = ctxs[0]->nCTA;
+  if (n_chains > b->sms) {
+    delete b;
+    return MC_ERR_ARG;  // every chain needs at least one CTA
+  }
+  b->nf_cols = 4;
+  std::vector<double> w(n_chains);
+  for (int i = 0; i < n_chains; i++) w[i] = (double)(ctxs[i]->h.L - ctxs[i]->h.lmin + 1);
+  b->ctas = split_by_weight(w, b->sms);
+  bool ok = cudaMalloc((void**)&b->d_systems, sizeof(McSys*) * n_chains) == cudaSuccess &&
+            cudaMalloc((void**)&b->d_rps, sizeof(RunParams) * n_chains) == cudaSuccess &&
+            cudaMalloc((void**)&b->d_cta_chain, sizeof(int) * b->sms) == cudaSuccess &&
+            cudaMalloc((void**)&b->d_cta_rank, sizeof(int) * b->sms) == cudaSuccess &&
+            cudaMalloc((void**)&b->d_chain_ctas, sizeof(int) * n_chains) == cudaSuccess;
+  if (!ok) {
+    mc_batch_destroy(b);
+    return MC_ERR_NOMEM;
+  }
+  std::vector<const McSys*> sp(n_chains);
+  std::vector<RunParams> rp(n_chains);
+  for (int i = 0; i < n_chains; i++) {
+    sp[i] = ctxs[i]->d_sys;
+    memset(&rp[i], 0, sizeof(RunParams));
+    rp[i].step0 = ctxs[i]->steps_total;
+  }
+  if (cudaMemcpy(b->d_systems, sp.data(), sizeof(McSys*) * n_chains, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_rps, rp.data(), sizeof(RunParams) * n_chains, cudaMemcpyHostToDevice) != cudaSuccess) {
+    mc_batch_destroy(b);
+    return MC_ERR_CUDA;
+  }
+  int rc = batch_upload_map(b);
+  if (rc != MC_OK) {
+    mc_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return MC_OK;
+}
+
+void mc_batch_destroy(mc_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->dev);
+  cudaStreamSynchronize(b->stream);
+  if (b->g_valid) cudaGraphExecDestroy(b->gexec);
+  cudaFree(b->d_systems);
+  cudaFree(b->d_rps);
+  cudaFree(b->d_cta_chain);
+  cudaFree(b->d_cta_rank);
+  cudaFree(b->d_chain_ctas);
+  delete b;
+}
+
+int mc_batch_info(mc_batch* b, int* ctas_out, int* nf_cols_out) {
+  if (!b) return MC_ERR_ARG;
+  if (ctas_out)
+    for (int i = 0; i < b->n; i++) ctas_out[i] = b->ctas[i];
+  if (nf_cols_out) *nf_cols_out = b->nf_cols;
+  return MC_OK;
+}
+
+int mc_batch_run(mc_batch* b, int64_t n_steps, const uint64_t* seeds, double beta, double half_width,
+                 mc_stats* stats, int64_t* log_j, double* log_dE, uint8_t* log_acc) {
+  if (!b || !seeds || n_steps < 0 || !(half_width >= 0.0) || !isfinite(beta)) return MC_ERR_ARG;
+  if ((log_j || log_dE || log_acc) && !(log_j && log_dE && log_acc)) return MC_ERR_ARG;
+  if (n_steps == 0) return MC_OK;
+  CK(cudaSetDevice(b->dev));
+  const bool logging = log_j != nullptr;
+  int rc = MC_OK;
+  if (logging) {
+    const size_t tot = (size_t)b->n * n_steps;
+    long long* dj = nullptr;
+    double* dd = nullptr;
+    unsigned char* da = nullptr;
+    if (cudaMalloc(&dj, sizeof(long long) * tot) != cudaSuccess ||
+        cudaMalloc(&dd, sizeof(double) * tot) != cudaSuccess || cudaMalloc(&da, tot) != cudaSuccess) {
+      cudaFree(dj);
+      cudaFree(dd);
+      cudaFree(da);
+      return MC_ERR_NOMEM;
+    }
+    std::vector<long long*> pj(b->n);
+    std::vector<double*> pd(b->n);
+    std::vector<unsigned char*> pa(b->n);
+    for (int i = 0; i < b->n; i++) {
+      pj[i] = dj + (size_t)i * n_steps;
+      pd[i] = dd + (size_t)i * n_steps;
+      pa[i] = da + (size_t)i * n_steps;
+    }
+    rc = batch_set_params(b, n_steps, seeds, beta, half_width, pj.data(), pd.data(), pa.data());
+    if (rc == MC_OK) rc = batch_enqueue(b);
+    if (rc == MC_OK) rc = batch_collect(b, stats, nullptr);
+    if (rc == MC_OK) {
+      std::vector<long long> tj(tot);
+      if (cudaMemcpy(tj.data(), dj, sizeof(long long) * tot, cudaMemcpyDeviceToHost) != cudaSuccess ||
+          cudaMemcpy(log_dE, dd, sizeof(double) * tot, cudaMemcpyDeviceToHost) != cudaSuccess ||
+          cudaMemcpy(log_acc, da, tot, cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = MC_ERR_CUDA;
+      for (size_t k = 0; k < tot; k++) log_j[k] = tj[k];
+    }
+    cudaFree(dj);
+    cudaFree(dd);
+    cudaFree(da);
+    b->seeds_valid = 0;
+    return rc;
+  }
+  // graph path: parameters live in device memory, the step counters advance there
+  const bool same_seeds =
+      b->seeds_valid && std::equal(b->seeds.begin(), b->seeds.end(), seeds);
+  if (!(b->g_valid && b->g_steps == n_steps && b->g_beta == beta && b->g_h == half_width &&
+        same_seeds)) {
+    rc = batch_set_params(b, n_steps, seeds, beta, half_width, nullptr, nullptr, nullptr);
+    if (rc != MC_OK) return rc;
+    b->seeds.assign(seeds, seeds + b->n);
+    b->seeds_valid = 1;
+    if (b->g_valid) {
+      cudaGraphExecDestroy(b->gexec);
+      b->g_valid = 0;
+    }
+    cudaStream_t cs = b->stream;
+    bool own = false;
+    if (!cs) {
+      // legacy stream cannot be captured: capture on a private stream
+      CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      own = true;
+    }
+    cudaStream_t saved = b->stream;
+    b->stream = cs;
+    cudaGraph_t graph;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      b->stream = saved;
+      if (own) cudaStreamDestroy(cs);
+      return MC_ERR_CUDA;
+    }
+    rc = batch_enqueue(b);
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    b->stream = saved;
+    if (own) cudaStreamDestroy(cs);
+    if (rc != MC_OK || e != cudaSuccess) return MC_ERR_CUDA;
+    e = cudaGraphInstantiate(&b->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return MC_ERR_CUDA;
+    b->g_valid = 1;
+    b->g_steps = n_steps;
+    b->g_beta = beta;
+    b->g_h = half_width;
+  }
+  CK(cudaGraphLaunch(b->gexec, b->stream));
+  if (!stats) {
+    for (int i = 0; i < b->n; i++) b->ctxs[i]->steps_total += n_steps;
+    return MC_OK;
+  }
+  return batch_collect(b, stats, nullptr);
+}
+
+int mc_batch_tune(mc_batch* b, int64_t trial_steps, double beta, double half_width) {
+  if (!b || trial_steps < 1) return MC_ERR_ARG;
+  CK(cudaSetDevice(b->dev));
+  std::vector<uint64_t> seeds(b->n);
+  for (int i = 0; i < b->n; i++) seeds[i] = 0x5EEDULL + i;
+  std::vector<long long> ns(b->n);
+  // time per proposal of every chain at 1 and 2 CTAs per chain
+  std::vector<double> t1(b->n), t2(b->n);
+  const int saved_nf = b->nf_cols;
+  for (int g = 1; g <= 2; g++) {
+    if (b->n * g > b->sms) {
+      // not enough SMs for a uniform g: reuse g = 1
+      for (int i = 0; i < b->n; i++) t2[i] = t1[i];
+      break;
+    }
+    b->ctas.assign(b->n, g);
+    int rc = batch_upload_map(b);
+    if (rc != MC_OK) return rc;
+    rc = batch_set_params(b, trial_steps, seeds.data(), beta, half_width, nullptr, nullptr, nullptr);
+    if (rc == MC_OK) rc = batch_enqueue(b);
+    if (rc == MC_OK) rc = batch_collect(b, nullptr, &ns);
+    if (rc != MC_OK) return rc;
+    for (int i = 0; i < b->n; i++) (g == 1 ? t1 : t2)[i] = (double)ns[i] / (double)trial_steps;
+  }
+  // model t(g) = a + b/g from the two points; greedy: give the next CTA to
+  // the chain with the largest predicted time
+  std::vector<double> A(b->n), B(b->n);
+  for (int i = 0; i < b->n; i++) {
+    B[i] = std::max(0.0, 2.0 * (t1[i] - t2[i]));
+    A[i] = std::max(0.0, t1[i] - B[i]);
+  }
+  std::vector<int> g(b->n, 1);
+  for (int left = b->sms - b->n; left > 0; left--) {
+    int worst = 0;
+    double wt = -1.0;
+    for (int i = 0; i < b->n; i++) {
+      const double ti = A[i] + B[i] / g[i];
+      if (ti > wt) {
+        wt = ti;
+        worst = i;
+      }
+    }
+    g[worst]++;
+  }
+  b->ctas = g;
+  int rc = batch_upload_map(b);
+  if (rc != MC_OK) return rc;
+  // far-field tiles: pick the count with the shortest slowest chain
+  int best_nf = saved_nf;
+  double best = 1e300;
+  for (int nf : {1, 2, 4, 8, 16}) {
+    b->nf_cols = nf;
+    rc = batch_set_params(b, trial_steps, seeds.data(), beta, half_width, nullptr, nullptr, nullptr);
+    if (rc == MC_OK) rc = batch_enqueue(b);
+    if (rc == MC_OK) rc = batch_collect(b, nullptr, &ns);
+    if (rc != MC_OK) return rc;
+    const double mk = (double)*std::max_element(ns.begin(), ns.end());
+    if (mk < best) {
+      best = mk;
+      best_nf = nf;
+    }
+  }
+  b->nf_cols = best_nf;
+  b->seeds_valid = 0;
+  if (b->g_valid) {
+    cudaGraphExecDestroy(b->gexec);
+    b->g_valid = 0;
+  }
   return MC_OK;
 }
 

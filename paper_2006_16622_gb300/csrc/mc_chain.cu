@@ -65,8 +65,8 @@ constexpr double kInf = __builtin_huge_val();
 }  // namespace
 
 template <typename TE>
-__global__ void __launch_bounds__(MC_THREADS, 1)
-    mc_chain_kernel(const McSys* __restrict__ sysp, RunParams rp) {
+__device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunParams& rp,
+                                           const int nCTA, const int cta) {
   __shared__ McSys S;
   __shared__ HarmTabs<TE> tabs;
   __shared__ unsigned short il[8][189];
@@ -91,7 +91,6 @@ __global__ void __launch_bounds__(MC_THREADS, 1)
   }
   __syncthreads();
 
-  const int nCTA = gridDim.x, cta = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int half = lane >> 4, hm = lane & 15;
   const int p = S.p, C = S.C, L = S.L;
@@ -102,6 +101,7 @@ __global__ void __launch_bounds__(MC_THREADS, 1)
   const bool prof_on = rp.prof != nullptr;
   const bool prof_lead = prof_on && cta == 0 && threadIdx.x == 0;
   unsigned long long tp0 = 0, tp1 = 0;
+  const unsigned long long t_begin = mc_globaltimer();
 
   for (long long t = 0; t < rp.nsteps; t++) {
     const int buf = (int)(t & 1);
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(MC_THREADS, 1)
       bool out = false;
       if (rp.mode == 0) {
         double d = 0.0;
-        mc_proposal_axis(rp.seed, (unsigned long long)(rp.step0 + t), 0u, S.n, rp.h,
+        mc_proposal_axis(rp.seed, (unsigned long long)(rp.step0 + t), rp.chain, S.n, rp.h,
                          lane < 3 ? lane : 0, &j, &d, lane == 3 ? &uu : nullptr);
         if (lane < 3) {
           const double4 pj = ldcg4(&S.ppos[j]);
@@ -180,7 +180,8 @@ __global__ void __launch_bounds__(MC_THREADS, 1)
     const int nE = L - S.lmin + 1;
     const int nN = same ? 27 : 54;
     const int nRB = (C + 31) / 32;
-    const int nF = pbc ? nRB * MC_NF_COLS : 0;
+    const int nfc = rp.nf_cols;
+    const int nF = pbc ? nRB * nfc : 0;
     const int nItems = nE + nN + nF + 2;  // + X + U
     double* part = S.partials + buf * MC_MAX_ITEMS;
 
@@ -316,7 +317,7 @@ __global__ void __launch_bounds__(MC_THREADS, 1)
         // ---- F: far lattice, Sec. 3.3 (iv) in the factored form
         //   dU_inf = sum_k W_k dK_k (H_k + 1/2 (G dK)_k),  W = 1 (m = 0) or 2
         const int f = it - nE - nN;
-        const int rb = f / MC_NF_COLS, cb = f % MC_NF_COLS;
+        const int rb = f / nfc, cb = f % nfc;
         const int m = hm;
         const double* x = half ? g.rn : g.r;
         const double c1 = 0.5 * S.a;
@@ -335,7 +336,7 @@ __global__ void __launch_bounds__(MC_THREADS, 1)
           }
         });
         __syncwarp();
-        const int csz = (C + MC_NF_COLS - 1) / MC_NF_COLS;
+        const int csz = (C + nfc - 1) / nfc;
         const int cbeg = cb * csz, cend = min(C, cbeg + csz);
         const int k = rb * 32 + lane;
         double contrib = 0.0;
@@ -536,12 +537,13 @@ __global__ void __launch_bounds__(MC_THREADS, 1)
           double gv[MC_NF_COLS];
 #pragma unroll
           for (int cb = 0; cb < MC_NF_COLS; cb++)
-            gv[cb] = __ldcg(&S.gK[(size_t)buf * MC_NF_COLS * C + (size_t)cb * C + k]);
+            gv[cb] = cb < nfc ? __ldcg(&S.gK[(size_t)buf * MC_NF_COLS * C + (size_t)cb * C + k]) : 0.0;
           const double dk = __ldcg(&S.dK[(size_t)buf * C + k]);
           const double kh = __ldcg(&S.Khat[k]), hh = __ldcg(&S.Hhat[k]);
           double gs = 0.0;
 #pragma unroll
-          for (int cb = 0; cb < MC_NF_COLS; cb++) gs += gv[cb];
+          for (int cb = 0; cb < MC_NF_COLS; cb++)
+            if (cb < nfc) gs += gv[cb];
           __stcg(&S.Khat[k], kh + dk);
           __stcg(&S.Hhat[k], hh + gs);
         }
@@ -711,18 +713,71 @@ __global__ void __launch_bounds__(MC_THREADS, 1)
     S.stats[0] = steps_done;
     S.stats[1] = n_acc;
     S.stats[2] = n_border;
+    S.stats[3] = (long long)(mc_globaltimer() - t_begin);  // this launch's wall time, ns
+  }
+}
+
+// one chain on the whole grid
+template <typename TE>
+__global__ void __launch_bounds__(MC_THREADS, 1)
+    mc_chain_kernel(const McSys* __restrict__ sysp, RunParams rp) {
+  chain_body<TE>(sysp, rp, (int)gridDim.x, (int)blockIdx.x);
+}
+
+// many independent chains: CTA b runs chain cta_chain[b] as rank cta_rank[b]
+// of that chain's group of chain_ctas[chain] CTAs (each chain has its own
+// barrier counter, partials and status in its McSys); per-chain parameters
+// in device memory, step counter advanced in place so that a replayed graph
+// continues every chain's proposal stream
+template <typename TE>
+__global__ void __launch_bounds__(MC_THREADS, 1)
+    mc_batch_kernel(const McSys* const* __restrict__ systems, RunParams* __restrict__ rps,
+                    const int* __restrict__ cta_chain, const int* __restrict__ cta_rank,
+                    const int* __restrict__ chain_ctas) {
+  const int ch = cta_chain[blockIdx.x];
+  RunParams rp = rps[ch];
+  const McSys* sys = systems[ch];
+  chain_body<TE>(sys, rp, chain_ctas[ch], cta_rank[blockIdx.x]);
+  if (cta_rank[blockIdx.x] == 0 && threadIdx.x == 0) {
+    // every CTA of the group read rps[ch] before the group's first barrier
+    const long long done = sys->stats[0];
+    if (done > 0) rps[ch].step0 = rp.step0 + done;
   }
 }
 
 template __global__ void mc_chain_kernel<double>(const McSys*, RunParams);
 template __global__ void mc_chain_kernel<float>(const McSys*, RunParams);
+template __global__ void mc_batch_kernel<double>(const McSys* const*, RunParams*, const int*,
+                                                 const int*, const int*);
+template __global__ void mc_batch_kernel<float>(const McSys* const*, RunParams*, const int*,
+                                                const int*, const int*);
 
-// host-side launcher (cooperative launch: all CTAs co-resident)
+// host-side launchers (cooperative launches: all CTAs co-resident)
 cudaError_t mc_launch_chain(const McSys* d_sys, const RunParams& rp, int prec, int nCTA,
                             cudaStream_t stream) {
   void* args[] = {(void*)&d_sys, (void*)&rp};
   const void* fn = prec ? (const void*)mc_chain_kernel<float> : (const void*)mc_chain_kernel<double>;
   return cudaLaunchCooperativeKernel(fn, dim3(nCTA), dim3(MC_THREADS), args, 0, stream);
+}
+
+cudaError_t mc_launch_batch(const McSys* const* d_systems, RunParams* d_rps, const int* d_cta_chain,
+                            const int* d_cta_rank, const int* d_chain_ctas, int prec, int nCTA,
+                            cudaStream_t stream) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nCTA);
+  cfg.blockDim = dim3(MC_THREADS);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (prec)
+    return cudaLaunchKernelEx(&cfg, mc_batch_kernel<float>, d_systems, d_rps, d_cta_chain,
+                              d_cta_rank, d_chain_ctas);
+  return cudaLaunchKernelEx(&cfg, mc_batch_kernel<double>, d_systems, d_rps, d_cta_chain,
+                            d_cta_rank, d_chain_ctas);
 }
 
 int mc_chain_max_ctas(int prec) {

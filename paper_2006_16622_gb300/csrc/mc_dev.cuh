@@ -29,7 +29,7 @@
 #define MC_WARPS (MC_THREADS / 32)
 #define MC_MAX_ITEMS 256
 #define MC_NF_ROWS 6    // far-field row blocks of 32 rows (covers C <= 192)
-#define MC_NF_COLS 16   // far-field column chunks
+#define MC_NF_COLS 16   // far-field column chunks (maximum; RunParams.nf_cols <= this)
 
 // ---------------------------------------------------------------- state
 struct McSys {
@@ -75,6 +75,8 @@ struct RunParams {
   unsigned char* log_acc;
   long long wait_ns;
   unsigned long long* prof;  // optional phase/item timers (see mc_chain.cu), may be null
+  int nf_cols;               // far-field column blocks per row block, 1..MC_NF_COLS
+  unsigned chain;            // Philox counter word 2 (chain id)
 };
 
 // ------------------------------------------------------------ error codes

@@ -23,7 +23,8 @@ SETUP_P2L = 0
 EXPORTED = ["mc_init", "mc_setup", "mc_propose", "mc_accept", "mc_run", "mc_energy",
             "mc_energy_fresh", "mc_get_positions", "mc_get_local", "mc_get_far",
             "mc_lattice_sums", "mc_status", "mc_set_wait_limit", "mc_profile", "mc_profile_read",
-            "mc_destroy", "mc_strerror", "mc_p2l_level_noalloc"]
+            "mc_destroy", "mc_strerror", "mc_p2l_level_noalloc", "mc_batch_create",
+            "mc_batch_tune", "mc_batch_run", "mc_batch_info", "mc_batch_destroy"]
 
 
 class McStats(ctypes.Structure):
@@ -68,10 +69,16 @@ def load(path: str = LIB_PATH):
     L.mc_p2l_level_noalloc.argtypes = [P, P, I64, D, I, I, I, I, P, P]
     L.mc_destroy.argtypes = [P]
     L.mc_destroy.restype = None
+    L.mc_batch_create.argtypes = [ctypes.POINTER(P), I, P]
+    L.mc_batch_tune.argtypes = [P, I64, D, D]
+    L.mc_batch_run.argtypes = [P, I64, P, D, D, P, P, P, P]
+    L.mc_batch_info.argtypes = [P, P, P]
+    L.mc_batch_destroy.argtypes = [P]
+    L.mc_batch_destroy.restype = None
     L.mc_strerror.argtypes = [I]
     L.mc_strerror.restype = ctypes.c_char_p
     for name in EXPORTED:
-        if name not in ("mc_destroy", "mc_strerror"):
+        if name not in ("mc_destroy", "mc_strerror", "mc_batch_destroy"):
             getattr(L, name).restype = I
     _lib = L
     return L
@@ -203,3 +210,55 @@ class Context:
 
     def set_wait_limit(self, ns):
         _check(load().mc_set_wait_limit(self._h, int(ns)), "mc_set_wait_limit")
+
+
+class Batch:
+    """Many independent chains in one persistent launch (the contexts keep
+    their systems; close the batch before the contexts)."""
+
+    def __init__(self, contexts):
+        L = load()
+        self.contexts = list(contexts)
+        arr = (ctypes.c_void_p * len(self.contexts))(*[c._h.value for c in self.contexts])
+        h = ctypes.c_void_p()
+        _check(L.mc_batch_create(ctypes.byref(h), len(self.contexts),
+                                 ctypes.cast(arr, ctypes.c_void_p)), "mc_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().mc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def tune(self, trial_steps=500, beta=1.0, half_width=0.3):
+        _check(load().mc_batch_tune(self._h, int(trial_steps), float(beta), float(half_width)),
+               "mc_batch_tune")
+
+    def info(self):
+        ctas = np.zeros(len(self.contexts), dtype=np.int32)
+        nf = np.zeros(1, dtype=np.int32)
+        _check(load().mc_batch_info(self._h, _ptr(ctas), _ptr(nf)), "mc_batch_info")
+        return ctas, int(nf[0])
+
+    def run(self, n_steps, seeds, beta=1.0, half_width=0.3, stats=True, log=False):
+        n = len(self.contexts)
+        seeds = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64))
+        st = (McStats * n)() if stats else None
+        lj = np.zeros((n, n_steps), dtype=np.int64) if log else None
+        ld = np.zeros((n, n_steps)) if log else None
+        la = np.zeros((n, n_steps), dtype=np.uint8) if log else None
+        _check(load().mc_batch_run(self._h, int(n_steps), _ptr(seeds), float(beta),
+                                   float(half_width), ctypes.cast(st, ctypes.c_void_p) if stats
+                                   else None, _ptr(lj), _ptr(ld), _ptr(la)), "mc_batch_run")
+        out = {}
+        if stats:
+            out["stats"] = [{k: getattr(st[i], k) for k, _ in McStats._fields_} for i in range(n)]
+        if log:
+            out.update(j=lj, dE=ld, acc=la)
+        return out

@@ -1,0 +1,79 @@
+"""Parity at the benchmark's full size and launch configuration.
+
+The N=1e5 workload (density 0.1, a=100, 5 levels, p=12, h=0.3, beta=1) as
+bench.py times it (one persistent launch over all SMs): the oracle sets the
+same system up (about a minute of one host core), then
+  - sampled cells of every level's expansions agree within 1e-12,
+  - the first 300 proposals of the seed-0 chain agree: every dE within
+    1e-10 max(1, |dE|) and every decision identical,
+  - properties that hold at any size: the running energy stays within
+    truncation of a fresh evaluation, and a fresh GPU setup on the final
+    positions equals the incrementally updated expansions.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2006_16622_gb300 import mcfmm
+from paper_2006_16622_gb300.workloads import LARGE
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def large_pair():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    W = LARGE
+    pos, q = W.system()
+    g = mcfmm.Context(pos, q, W.a, W.levels, W.p, precision=mcfmm.FP64)
+    g.setup()
+    o = O.System(pos, q, W.a, W.levels, W.p)
+    o.setup()
+    yield W, g, o, pos, q
+    g.close()
+
+
+def test_large_setup_sampled_cells(large_pair):
+    W, g, o, pos, q = large_pair
+    rng = np.random.default_rng(0)
+    for lev in range(2, W.levels + 1):
+        A, B = g.local(lev), o.local(lev)
+        cells = rng.choice(len(B), size=min(len(B), 64), replace=False)
+        scale = np.max(np.abs(B))
+        assert np.max(np.abs(A[cells] - B[cells])) <= 1e-12 * scale, lev
+    Kg, Hg = g.far()
+    Ko, Ho = o.KH()
+    assert np.max(np.abs(Kg - Ko)) <= 1e-12 * np.max(np.abs(Ko))
+    assert abs(g.energy() - o.energy()) <= 1e-10 * abs(o.energy())
+
+
+def test_large_replayed_chain(large_pair):
+    W, g, o, pos, q = large_pair
+    steps = 300
+    rg = g.run(steps, seed=W.seed, beta=W.beta, half_width=W.half_width, log=True)
+    ro = o.run(steps, seed=W.seed, step0=0, beta=W.beta, half_width=W.half_width)
+    assert ro["n_borderline"] == 0 and rg["borderline"] == 0
+    assert np.array_equal(rg["j"], ro["j"])
+    err = np.abs(rg["dE"] - ro["dE"]) / np.maximum(1.0, np.abs(ro["dE"]))
+    assert np.max(err) <= 1e-10, np.max(err)
+    assert np.array_equal(rg["acc"], ro["acc"])
+    assert np.array_equal(g.positions(), o.positions())
+    assert abs(g.energy() - o.energy()) <= 1e-9 * abs(o.energy())
+
+
+def test_large_properties_after_a_long_chain(large_pair):
+    W, g, o, pos, q = large_pair
+    g.run(20_000, seed=W.seed + 1, beta=W.beta, half_width=W.half_width)
+    fresh = g.energy_fresh()
+    # truncation-level difference between running and fresh energies
+    assert abs(g.energy() - fresh) <= 1e-6 * abs(fresh)
+    f = mcfmm.Context(g.positions(), q, W.a, W.levels, W.p)
+    f.setup()
+    for lev in range(2, W.levels + 1):
+        A, B = g.local(lev), f.local(lev)
+        assert np.max(np.abs(A - B)) <= 1e-11 * np.max(np.abs(B)), lev
+    f.close()
