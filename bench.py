@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=3000, help="oracle proposals timed")
+    ap.add_argument("--batch-steps", type=int, default=5000, help="proposals per chain per batched step")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
     return ap.parse_args()
 
 
@@ -205,6 +208,94 @@ def read_profile_traffic():
     return None
 
 
+def batched_form(args, precision, stream, flush):
+    """64 independent chains, N log-uniform in [1000, 50000] at density 0.1,
+    ~20 charges per finest cell, p=10, h=0.3, beta=1, seed i for chain i; one
+    autotuned persistent launch per step, replayed from a CUDA graph."""
+    import numpy as np
+    import torch
+
+    from paper_2006_16622_gb300 import mcfmm
+    from paper_2006_16622_gb300.workloads import batched_systems, uniform_system
+
+    systems = batched_systems(64, 1000, 50000, 0.1, 20.0)
+    ctxs = []
+    t0 = time.perf_counter()
+    for n, a, L, i in systems:
+        pos, q = uniform_system(n, a, seed=1000 + i)
+        c = mcfmm.Context(pos, q, a, L, 10, precision=precision, stream=stream.cuda_stream)
+        c.setup()
+        ctxs.append(c)
+    setup_s = time.perf_counter() - t0
+    b = mcfmm.Batch(ctxs)
+    t0 = time.perf_counter()
+    b.tune(trial_steps=300, beta=1.0, half_width=0.3)
+    tune_s = time.perf_counter() - t0
+    ctas, nf = b.info()
+    seeds = np.arange(len(ctxs), dtype=np.uint64)
+    Sb = args.batch_steps
+    for _ in range(args.warmup):
+        b.run(Sb, seeds, beta=1.0, half_width=0.3, stats=False)
+    torch.cuda.synchronize()
+    durs = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.run(Sb, seeds, beta=1.0, half_width=0.3, stats=False)
+        e1.record(stream)
+        e1.synchronize()
+        durs.append(e0.elapsed_time(e1) / 1000.0)
+    st = b.run(200, seeds, beta=1.0, half_width=0.3)["stats"]
+    acc = sum(x["accepted"] for x in st) / max(1, sum(x["steps"] for x in st))
+    b.close()
+    for c in ctxs:
+        if c.status() != 0:
+            raise RuntimeError("batched chain failed")
+        c.close()
+    return dict(value=len(ctxs) * Sb * args.steps / sum(durs), setup_s=setup_s, tune_s=tune_s,
+                ctas=[int(x) for x in ctas], nf_cols=nf, acceptance=acc,
+                sizes=[n for n, _, _, _ in systems])
+
+
+def precision_form_stats(W, stream):
+    """FP32-eval vs the (oracle-parity-tested) FP64 chain on the same seed:
+    per-proposal dE error over the common prefix of the two chains, and the
+    energy drift with a full FP64 re-setup every R accepts, next to the FP64
+    drift floor (P2L truncation asymmetry)."""
+    import numpy as np
+
+    from paper_2006_16622_gb300 import mcfmm
+    pos, q = W.system()
+    out = {}
+    M = 4000
+    logs = {}
+    for prec in (mcfmm.FP64, mcfmm.FP32_EVAL):
+        c = mcfmm.Context(pos, q, W.a, W.levels, W.p, precision=prec, stream=stream.cuda_stream)
+        c.setup()
+        logs[prec] = c.run(M, seed=77, beta=W.beta, half_width=W.half_width, log=True)
+        c.close()
+    a64, a32 = logs[mcfmm.FP64], logs[mcfmm.FP32_EVAL]
+    diff = np.nonzero(a64["acc"] != a32["acc"])[0]
+    k = int(diff[0]) if len(diff) else M
+    e = np.abs(a32["dE"][:k] - a64["dE"][:k])
+    e = e[np.isfinite(e)]
+    out.update(dE_err_p95=float(np.percentile(e, 95)), dE_err_max=float(e.max()),
+               dE_err_samples=int(len(e)), common_prefix=k)
+    R = 50_000
+    for name, prec in (("fp32_eval", mcfmm.FP32_EVAL), ("fp64_floor", mcfmm.FP64)):
+        c = mcfmm.Context(pos, q, W.a, W.levels, W.p, precision=prec, stream=stream.cuda_stream)
+        c.setup()
+        st = c.run(int(2.2 * R / 0.9), seed=78, beta=W.beta, half_width=W.half_width,
+                   resetup_every=R)
+        c.close()
+        out[f"drift_per_1e6_accepts_{name}"] = st["max_drift"] * 1e6 / R
+        out[f"resetups_{name}"] = st["resetups"]
+    out["resetup_every_accepts"] = R
+    return out
+
+
 def gpu_arm(args):
     import numpy as np
     import torch
@@ -279,6 +370,12 @@ def gpu_arm(args):
     r64 = time_form(mcfmm.FP64)
     r32 = None if args.no_fp32 else time_form(mcfmm.FP32_EVAL)
 
+    rb32 = rb64 = None
+    if not args.no_batch:
+        rb32 = batched_form(args, mcfmm.FP32_EVAL, stream, flush)
+        rb64 = batched_form(args, mcfmm.FP64, stream, flush)
+    prec_stats = None if args.no_precision else precision_form_stats(W, stream)
+
     # end to end through the C ABI: host arrays in, positions and energy out
     e2e = None
     if not args.no_e2e:
@@ -333,7 +430,18 @@ def gpu_arm(args):
         forms["fp32_eval"] = world * S * args.steps / r32["total"]
         forms["fp32_eval_acceptance"] = r32["nu"]
         forms["fp32_eval_setup_s"] = r32["setup_s"]
-    forms["batched"] = None
+    if rb32:
+        forms["batched_fp32_eval"] = world * rb32["value"]
+        forms["batched_fp64"] = world * rb64["value"]
+        forms["batched_config"] = {
+            "workload": "64 chains, N log-uniform [1000, 50000], rho=0.1, ~20 per finest cell, "
+                        "p=10, h=0.3, beta=1, seed i for chain i",
+            "proposals_per_chain_per_step": args.batch_steps, "ctas_per_chain": rb32["ctas"],
+            "nf_cols": rb32["nf_cols"], "ctas_per_chain_fp64": rb64["ctas"],
+            "nf_cols_fp64": rb64["nf_cols"], "setup_s": rb32["setup_s"], "tune_s": rb32["tune_s"],
+            "acceptance": rb32["acceptance"]}
+    else:
+        forms["batched_fp32_eval"] = None
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * r64["total"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -343,6 +451,7 @@ def gpu_arm(args):
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": args.steps, "clocks": r64["clocks"], "forms": forms,
+            "precision_form": prec_stats,
             "setup_s": r64["setup_s"]}
     print(json.dumps(line), flush=True)
     if dist is not None:

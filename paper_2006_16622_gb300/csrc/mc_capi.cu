@@ -8,6 +8,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
 #include <vector>
 
 #include "../../include/mcfmm.h"
@@ -157,6 +160,34 @@ int energy_into(mc_ctx* c, double* d_dst) {
   CK(cudaGetLastError());
   k_energy_finish<<<1, 256, 0, c->stream>>>(c->d_sys, nw, c->d_scratch, d_dst);
   CK(cudaGetLastError());
+  return MC_OK;
+}
+
+// The unit-lattice sums depend only on lmax: one device table per (device,
+// lmax), computed on first use and kept for the life of the process
+// (2 (lmax+1)^2 doubles each).
+std::map<std::pair<int, int>, double*> g_lattice_cache;
+std::mutex g_lattice_mutex;
+
+int lattice_table(int dev, int lmax, cudaStream_t stream, const double** out) {
+  std::lock_guard<std::mutex> lock(g_lattice_mutex);
+  auto it = g_lattice_cache.find({dev, lmax});
+  if (it != g_lattice_cache.end()) {
+    *out = it->second;
+    return MC_OK;
+  }
+  double* d = nullptr;
+  if (cudaMalloc(&d, sizeof(double) * 2 * (lmax + 1) * (lmax + 1)) != cudaSuccess) {
+    cudaGetLastError();
+    return MC_ERR_NOMEM;
+  }
+  k_lattice_sums<<<(lmax + 1) * (lmax + 2) / 2, 256, 0, stream>>>(lmax, d);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(stream) != cudaSuccess) {
+    cudaFree(d);
+    return MC_ERR_CUDA;
+  }
+  g_lattice_cache[{dev, lmax}] = d;
+  *out = d;
   return MC_OK;
 }
 
@@ -335,10 +366,12 @@ int mc_init(mc_ctx** out, int64_t n, const double* pos, const double* q, double 
   DA(c->d_scratch, sizeof(double) * need);
 
   if (bc == MC_BC_PBC) {
-    const int lmax = 2 * p;
-    double* d_st = nullptr;
-    DA(d_st, sizeof(double) * 2 * (lmax + 1) * (lmax + 1));
-    k_lattice_sums<<<(lmax + 1) * (lmax + 2) / 2, 256, 0, c->stream>>>(lmax, d_st);
+    const double* d_st = nullptr;
+    rc = lattice_table(c->dev, 2 * p, c->stream, &d_st);
+    if (rc != MC_OK) {
+      mc_destroy(c);
+      return rc;
+    }
     k_far_operator<<<grid_for(c->sms, (size_t)C * C, 256), 256, 0, c->stream>>>(p, box, d_st, h.G);
     DCK(cudaGetLastError());
   }

@@ -368,13 +368,13 @@ __global__ void k_energy_finish(const McSys* __restrict__ sysp, int nw, const do
 // Scaled lattice sums St_l^mu = sum_{max|v_i| >= 2} It_l^mu(v) over the unit
 // lattice (It the scaled irregular harmonic; St = s_l,mu S_l^mu).  Images are
 // summed in cubic shells: l = 1, 2 vanish by cubic symmetry and l = 0 only
-// meets the total charge (zero), so l < 3 is 0.  For 3 <= l < 14 the sum
+// meets the total charge (zero), so l < 3 is 0.  For 3 <= l < 20 the sum
 // over all v != 0 is split (Poisson summation of the harmonic polynomial
 // h(x) = |x|^l Y(x), split at t = 2):
 //   sum_v h(v)/|v|^(2l+1) Q(l+1/2, 2 pi |v|^2)
 //   + pi^(l-1/2)/Gamma(l+1/2) (-i)^l sum_{k != 0} h(k) e^{-pi |k|^2 / 2} / |k|^2
-// and the 26 shell-1 terms are removed.  For l >= 14 shells 2..32 are summed
-// directly (tail below 1e-15 relative).  One block per (l, mu >= 0).
+// and the 26 shell-1 terms are removed.  For l >= 20 shells 2..20 are summed
+// directly (tail below 1e-17 relative).  One block per (l, mu >= 0).
 __device__ __forceinline__ void rt_single(int l, int mu, double x, double y, double z,
                                           double* re, double* im) {
   // scaled regular harmonic Rt_l^mu(x) via the diagonal then the column
@@ -414,7 +414,7 @@ __global__ void k_lattice_sums(int lmax, double* __restrict__ out /* complex (lm
   for (int k = 2; k <= l + mu; k++) fh *= k;
   const double s2 = fl * fh;  // h = s2 * Rt
   const double pi = 3.141592653589793;
-  if (l >= 3 && l < 14) {
+  if (l >= 3 && l < 20) {
     const int R = 7, K = 9;
     const int side = 2 * R + 1;
     for (int idx = threadIdx.x; idx < side * side * side; idx += blockDim.x) {
@@ -458,8 +458,8 @@ __global__ void k_lattice_sums(int lmax, double* __restrict__ out /* complex (lm
       sr += wgt * (ur * hr - ui * hi);
       si += wgt * (ur * hi + ui * hr);
     }
-  } else if (l >= 14) {
-    const int R = 32, side = 2 * R + 1;
+  } else if (l >= 20) {
+    const int R = 20, side = 2 * R + 1;
     for (int idx = threadIdx.x; idx < side * side * side; idx += blockDim.x) {
       const int x = idx / (side * side) - R, y = (idx / side) % side - R, z = idx % side - R;
       if (max(abs(x), max(abs(y), abs(z))) < 2) continue;
