@@ -119,6 +119,20 @@ int mc_get_far(mc_ctx *ctx, double *K_out, double *H_out);
  * Y_l^m(v/|v|)/|v|^(l+1), l <= lmax <= 30, as computed on the device;
  * complex interleaved, index 2*(l*l + l + m). */
 int mc_lattice_sums(int lmax, double *out);
+/* Schedule of mc_run / mc_batch_run chains.
+ *   MC_SCHEDULE_PHASED     (default) propose items, grid barrier, decision,
+ *                          accept items, grid barrier: two barriers per
+ *                          accepted step;
+ *   MC_SCHEDULE_PIPELINED  the accept of step k runs in the same phase as the
+ *                          proposal of step k+1 (one barrier per step); the
+ *                          proposal sees the accepted state through
+ *                          speculative coarse-level deltas and exact
+ *                          Legendre-series corrections.  Same results to
+ *                          roundoff; slower on GB300 in the measurements so
+ *                          far (contention of the merged phase). */
+#define MC_SCHEDULE_PHASED 0
+#define MC_SCHEDULE_PIPELINED 1
+int mc_set_schedule(mc_ctx *ctx, int schedule);
 /* Status of the last asynchronous launch (MC_OK, MC_ERR_TIMEOUT, ...). */
 int mc_status(mc_ctx *ctx);
 /* Wait-limit of the device-side grid barrier in nanoseconds (default 2e9);
@@ -164,6 +178,8 @@ int mc_batch_run(mc_batch *b, int64_t n_steps, const uint64_t *seeds, double bet
                  uint8_t *log_acc);
 /* CTAs given to each chain (n_chains ints) and the far-field tile count. */
 int mc_batch_info(mc_batch *b, int *ctas_out, int *nf_cols_out);
+/* Schedule of the batch's chains (MC_SCHEDULE_*, default phased). */
+int mc_batch_set_schedule(mc_batch *b, int schedule);
 void mc_batch_destroy(mc_batch *b);
 
 /* Size of the fixed device scratch of mc_p2l_level_noalloc, in doubles

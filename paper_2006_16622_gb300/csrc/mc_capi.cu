@@ -19,6 +19,11 @@
 // kernels defined in the other translation units
 cudaError_t mc_launch_chain(const McSys* d_sys, const RunParams& rp, int prec, int nCTA,
                             cudaStream_t stream);
+cudaError_t mc_launch_pipe(const McSys* d_sys, const RunParams& rp, int prec, int nCTA,
+                           cudaStream_t stream);
+cudaError_t mc_launch_batch_pipe(const McSys* const* d_systems, RunParams* d_rps,
+                                 const int* d_cta_chain, const int* d_cta_rank,
+                                 const int* d_chain_ctas, int prec, int nCTA, cudaStream_t stream);
 cudaError_t mc_launch_batch(const McSys* const* d_systems, RunParams* d_rps, const int* d_cta_chain,
                             const int* d_cta_rank, const int* d_chain_ctas, int prec, int nCTA,
                             cudaStream_t stream);
@@ -51,6 +56,7 @@ struct mc_ctx {
   size_t scratch_doubles;
   double* d_energy_tmp;  // fresh-energy target
   unsigned long long* d_prof;  // 32 timers when profiling is on, else null
+  int schedule;                // MC_SCHEDULE_*
   std::vector<void*> allocs;
 };
 
@@ -117,11 +123,19 @@ int sync_status(mc_ctx* c) {
 int launch_chain(mc_ctx* c, RunParams& rp) {
   rp.wait_ns = c->wait_ns;
   rp.prof = c->d_prof;
-  rp.nf_cols = MC_NF_COLS;
+  const bool piped = rp.mode == 0 && c->schedule == MC_SCHEDULE_PIPELINED;
+  rp.nf_cols = piped ? 4 : MC_NF_COLS;
   rp.chain = 0u;
   CK(cudaMemsetAsync(c->h.bar, 0, sizeof(unsigned long long), c->stream));
   CK(cudaMemsetAsync(c->h.status, 0, sizeof(int), c->stream));
-  CK(mc_launch_chain(c->d_sys, rp, c->h.prec, c->nCTA, c->stream));
+  if (piped) {
+    // accept of step k overlaps the proposal of k+1
+    CK(cudaMemsetAsync(c->h.sync, 0, sizeof(unsigned long long) * 16, c->stream));
+    CK(cudaMemsetAsync(c->h.dsmall, 0, sizeof(double) * 3 * (size_t)c->h.nsmall * c->h.C, c->stream));
+    CK(mc_launch_pipe(c->d_sys, rp, c->h.prec, c->nCTA, c->stream));
+  } else {
+    CK(mc_launch_chain(c->d_sys, rp, c->h.prec, c->nCTA, c->stream));
+  }
   return MC_OK;
 }
 
@@ -344,6 +358,19 @@ int mc_init(mc_ctx** out, int64_t n, const double* pos, const double* q, double 
   DA(h.stats, sizeof(long long) * 4);
   DA(h.result, sizeof(double) * 4);
   DA(c->d_energy_tmp, sizeof(double));
+  h.ls_end = h.L + 1;
+  for (int l = h.lmin; l <= h.L; l++)
+    if (h.lev_n[l] > 4) {
+      h.ls_end = l;
+      break;
+    }
+  h.nsmall = h.lev_off[h.ls_end > h.L ? h.L : h.ls_end] + (h.ls_end > h.L ? h.lev_n[h.L] * h.lev_n[h.L] * h.lev_n[h.L] : 0);
+  if (h.ls_end <= h.lmin) h.nsmall = 0;
+  DA(h.Hhat2, sizeof(double) * C);
+  DA(h.dipv2, sizeof(double) * 3);
+  DA(h.dsmall, sizeof(double) * 3 * (size_t)std::max(1, h.nsmall) * C);
+  DA(h.sync, sizeof(unsigned long long) * 16);
+  DCK(cudaMemsetAsync(h.dsmall, 0, sizeof(double) * 3 * (size_t)std::max(1, h.nsmall) * C, c->stream));
   DCK(cudaMemsetAsync(h.Khat, 0, sizeof(double) * C, c->stream));
   DCK(cudaMemsetAsync(h.Hhat, 0, sizeof(double) * C, c->stream));
   DCK(cudaMemsetAsync(h.G, 0, sizeof(double) * (size_t)C * C, c->stream));
@@ -652,6 +679,12 @@ int mc_profile_read(mc_ctx* c, uint64_t* out) {
   return MC_OK;
 }
 
+int mc_set_schedule(mc_ctx* c, int schedule) {
+  if (!c || (schedule != MC_SCHEDULE_PHASED && schedule != MC_SCHEDULE_PIPELINED)) return MC_ERR_ARG;
+  c->schedule = schedule;
+  return MC_OK;
+}
+
 int mc_status(mc_ctx* c) {
   if (!c) return MC_ERR_ARG;
   return sync_status(c);
@@ -673,6 +706,7 @@ struct mc_batch {
   cudaStream_t stream;
   std::vector<int> ctas;  // CTAs per chain
   int nf_cols;
+  int schedule;
   // device copies
   const McSys** d_systems;
   RunParams* d_rps;
@@ -764,9 +798,17 @@ int batch_enqueue(mc_batch* b) {
   for (int i = 0; i < b->n; i++) {
     CK(cudaMemsetAsync(b->ctxs[i]->h.bar, 0, sizeof(unsigned long long), b->stream));
     CK(cudaMemsetAsync(b->ctxs[i]->h.status, 0, sizeof(int), b->stream));
+    CK(cudaMemsetAsync(b->ctxs[i]->h.sync, 0, sizeof(unsigned long long) * 16, b->stream));
+    CK(cudaMemsetAsync(b->ctxs[i]->h.dsmall, 0,
+                       sizeof(double) * 3 * (size_t)b->ctxs[i]->h.nsmall * b->ctxs[i]->h.C, b->stream));
   }
-  CK(mc_launch_batch(b->d_systems, b->d_rps, b->d_cta_chain, b->d_cta_rank, b->d_chain_ctas,
-                     b->prec, b->nCTA, b->stream));
+  if (b->schedule == MC_SCHEDULE_PIPELINED) {
+    CK(mc_launch_batch_pipe(b->d_systems, b->d_rps, b->d_cta_chain, b->d_cta_rank,
+                            b->d_chain_ctas, b->prec, b->nCTA, b->stream));
+  } else {
+    CK(mc_launch_batch(b->d_systems, b->d_rps, b->d_cta_chain, b->d_cta_rank, b->d_chain_ctas,
+                       b->prec, b->nCTA, b->stream));
+  }
   return MC_OK;
 }
 
@@ -866,6 +908,16 @@ void mc_batch_destroy(mc_batch* b) {
   cudaFree(b->d_cta_rank);
   cudaFree(b->d_chain_ctas);
   delete b;
+}
+
+int mc_batch_set_schedule(mc_batch* b, int schedule) {
+  if (!b || (schedule != MC_SCHEDULE_PHASED && schedule != MC_SCHEDULE_PIPELINED)) return MC_ERR_ARG;
+  b->schedule = schedule;
+  if (b->g_valid) {
+    cudaGraphExecDestroy(b->gexec);
+    b->g_valid = 0;
+  }
+  return MC_OK;
 }
 
 int mc_batch_info(mc_batch* b, int* ctas_out, int* nf_cols_out) {

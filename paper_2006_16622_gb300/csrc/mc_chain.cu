@@ -92,7 +92,6 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
   __syncthreads();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int half = lane >> 4, hm = lane & 15;
   const int p = S.p, C = S.C, L = S.L;
   const bool pbc = (S.bc == 0);
   const int nWarpsTot = nCTA * MC_WARPS;
@@ -193,37 +192,37 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
         if (it == nItems - 2 && g.outside) partial = kInf;
         if (it == nItems - 1 && lane == 0 && rp.mode == 0) part[MC_MAX_ITEMS - 1] = log(u);
       } else if (it < nE) {
-        // ---- E: Eq. (2) at r (half 0) and r' (half 1) on level l
+        // ---- E: Eq. (2) at r (group 0) and r' (group 1) on level l
         const int l = L - it, sh = L - l;
-        const int* cc = half ? g.cfn : g.cf;
+        const int grp = lane >> 3, side = grp & 1;
+        const int* cc = side ? g.cfn : g.cf;
         const int cx = cc[0] >> sh, cy = cc[1] >> sh, cz = cc[2] >> sh;
         const int nl = S.lev_n[l];
         const double* Lb = S.Lhat + (size_t)(S.lev_off[l] + (cx * nl + cy) * nl + cz) * C;
-        const int m = hm;
-        double Ld[MC_PMAX + 1], Lid[MC_PMAX + 1];
+        double ld[MC_PMAX + 2], lid[MC_PMAX + 2];
 #pragma unroll
-        for (int n = 0; n <= MC_PMAX; n++) {
-          const bool on = n <= p && m <= n;
+        for (int t2 = 0; t2 <= MC_PMAX + 1; t2++) {
+          int n, m;
+          bool v;
+          group_nm(p, t2, &n, &m, &v);
           const int k = rl_re(n, m);
-          Ld[n] = on ? __ldcg(&Lb[k]) : 0.0;
-          Lid[n] = (on && m) ? __ldcg(&Lb[k + 1]) : 0.0;
+          ld[t2] = v ? __ldcg(&Lb[k]) : 0.0;
+          lid[t2] = (v && m) ? __ldcg(&Lb[k + 1]) : 0.0;
         }
-        TE Lr[MC_PMAX + 1], Li[MC_PMAX + 1];
+        TE Lr[MC_PMAX + 2], Li[MC_PMAX + 2];
 #pragma unroll
-        for (int n = 0; n <= MC_PMAX; n++) {
-          Lr[n] = from_double<TE>(Ld[n]);
-          Li[n] = from_double<TE>(Lid[n]);
+        for (int t2 = 0; t2 <= MC_PMAX + 1; t2++) {
+          Lr[t2] = from_double<TE>(ld[t2]);
+          Li[t2] = from_double<TE>(lid[t2]);
         }
-        const TE dx = from_double<TE>(s_off[half][l][0]), dy = from_double<TE>(s_off[half][l][1]),
-                 dz = from_double<TE>(s_off[half][l][2]);
+        const TE dx = from_double<TE>(s_off[side][l][0]), dy = from_double<TE>(s_off[side][l][1]),
+                 dz = from_double<TE>(s_off[side][l][2]);
         TE acc = TE(0);
-        regular_columns<TE>(&tabs, p, m, dx, dy, dz, [&](int n, TE cr, TE ci) {
-          if (n >= m) acc += Lr[n] * cr - Li[n] * ci;
+        regular_group<TE>(&tabs, p, dx, dy, dz, [&](int t2, int n, int m, bool v, TE vr, TE vi) {
+          if (v) acc += (m ? TE(2) : TE(1)) * (Lr[t2] * vr - Li[t2] * vi);
         });
-        if (m > p) acc = TE(0);
-        if (m > 0) acc *= TE(2);
-        acc = half_sum(acc);
-        const TE accn = __shfl_sync(0xffffffffu, acc, 16);
+        acc = group_sum(acc);
+        const TE accn = __shfl_sync(0xffffffffu, acc, 8);
         partial = g.q * to_double(accn - acc);
       } else if (it < nE + nN) {
         // ---- N: Alg. 1 over one near cell (27 cells of the extended domain)
@@ -318,21 +317,21 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
         //   dU_inf = sum_k W_k dK_k (H_k + 1/2 (G dK)_k),  W = 1 (m = 0) or 2
         const int f = it - nE - nN;
         const int rb = f / nfc, cb = f % nfc;
-        const int m = hm;
-        const double* x = half ? g.rn : g.r;
         const double c1 = 0.5 * S.a;
         double* st = stage[warp];
         const TE qe = from_double<TE>(g.q);
-        const TE dx = from_double<TE>(x[0] - c1), dy = from_double<TE>(x[1] - c1),
-                 dz = from_double<TE>(x[2] - c1);
-        regular_columns<TE>(&tabs, p, m, dx, dy, dz, [&](int n, TE cr, TE ci) {
-          const TE nr = __shfl_xor_sync(0xffffffffu, cr, 16);
-          const TE ni = __shfl_xor_sync(0xffffffffu, ci, 16);
-          if (half == 0 && m <= p && n >= m) {
+        const int grp = lane >> 3;
+        const double* xg = (grp & 1) ? g.rn : g.r;
+        const TE dx = from_double<TE>(xg[0] - c1), dy = from_double<TE>(xg[1] - c1),
+                 dz = from_double<TE>(xg[2] - c1);
+        regular_group<TE>(&tabs, p, dx, dy, dz, [&](int t2, int n, int m, bool v, TE vr, TE vi) {
+          const TE nr = __shfl_xor_sync(0xffffffffu, vr, 8);
+          const TE ni = __shfl_xor_sync(0xffffffffu, vi, 8);
+          if (grp == 0 && v) {
             // dK = q (conj Rt(r' - R1) - conj Rt(r - R1))
             const int k = rl_re(n, m);
-            st[k] = to_double(qe * (nr - cr));
-            if (m) st[k + 1] = to_double(-qe * (ni - ci));
+            st[k] = to_double(qe * (nr - vr));
+            if (m) st[k + 1] = to_double(-qe * (ni - vi));
           }
         });
         __syncwarp();
@@ -468,7 +467,7 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
       const bool samel = ((g.cf[0] >> sh) == (g.cfn[0] >> sh)) &&
                          ((g.cf[1] >> sh) == (g.cfn[1] >> sh)) &&
                          ((g.cf[2] >> sh) == (g.cfn[2] >> sh));
-      lev_items[l] = (nl <= 4) ? 189 : (samel ? 189 : 378);
+      lev_items[l] = (nl <= 4) ? 95 : (samel ? 189 : 378);
       lev_start[l] = nA;
       nA += lev_items[l];
     }
@@ -557,38 +556,40 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
       const int sh = L - l, nl = S.lev_n[l];
       const int co[3] = {g.cf[0] >> sh, g.cf[1] >> sh, g.cf[2] >> sh};
       const int cn[3] = {g.cfn[0] >> sh, g.cfn[1] >> sh, g.cfn[2] >> sh};
-      const int m = hm;
       if (nl <= 4) {
-        // entry k of this half's interaction list; image copies make targets
-        // repeat across entries, so the update goes through L2 atomic adds
-        const int* cs = half ? cn : co;
+        // entries 2k (groups 0, 1) and 2k+1 (groups 2, 3) of IL(alpha)
+        // (groups 0, 2) and IL(alpha') (groups 1, 3); image copies make
+        // targets repeat across entries, so the update uses L2 atomic adds
+        const int grp = lane >> 3, side = grp & 1;
+        const int entry = 2 * k + (grp >> 1);
+        const int* cs = side ? cn : co;
         const int par = ((cs[0] & 1) << 2) | ((cs[1] & 1) << 1) | (cs[2] & 1);
-        int ox, oy, oz;
-        il_unpack(il[par][k], &ox, &oy, &oz);
+        int ox = 0, oy = 0, oz = 0;
+        if (entry < 189) il_unpack(il[par][entry], &ox, &oy, &oz);
         const int e[3] = {cs[0] + ox, cs[1] + oy, cs[2] + oz};
-        const bool valid = pbc || (e[0] >= 0 && e[0] < nl && e[1] >= 0 && e[1] < nl &&
-                                   e[2] >= 0 && e[2] < nl);
+        const bool valid = entry < 189 && (pbc || (e[0] >= 0 && e[0] < nl && e[1] >= 0 &&
+                                                   e[1] < nl && e[2] >= 0 && e[2] < nl));
         const int t3[3] = {mc_wrap_coord(e[0], nl), mc_wrap_coord(e[1], nl),
                            mc_wrap_coord(e[2], nl)};
-        const TE f = valid ? from_double<TE>(half ? g.q : -g.q) : TE(0);
+        const TE f = valid ? from_double<TE>(side ? g.q : -g.q) : TE(0);
         TE dx = TE(3), dy = TE(3), dz = TE(3);
         if (valid) {
           if (sizeof(TE) == 8) {
-            dx = (TE)(s_off[half][l][0] - s_kw[l][ox + 3]);
-            dy = (TE)(s_off[half][l][1] - s_kw[l][oy + 3]);
-            dz = (TE)(s_off[half][l][2] - s_kw[l][oz + 3]);
+            dx = (TE)(s_off[side][l][0] - s_kw[l][ox + 3]);
+            dy = (TE)(s_off[side][l][1] - s_kw[l][oy + 3]);
+            dz = (TE)(s_off[side][l][2] - s_kw[l][oz + 3]);
           } else {
-            dx = from_double<TE>(s_off[half][l][0]) - s_kwe[l][ox + 3];
-            dy = from_double<TE>(s_off[half][l][1]) - s_kwe[l][oy + 3];
-            dz = from_double<TE>(s_off[half][l][2]) - s_kwe[l][oz + 3];
+            dx = from_double<TE>(s_off[side][l][0]) - s_kwe[l][ox + 3];
+            dy = from_double<TE>(s_off[side][l][1]) - s_kwe[l][oy + 3];
+            dz = from_double<TE>(s_off[side][l][2]) - s_kwe[l][oz + 3];
           }
         }
         double* Lt = S.Lhat + (size_t)(S.lev_off[l] + (t3[0] * nl + t3[1]) * nl + t3[2]) * C;
-        irregular_columns<TE>(&tabs, p, m, dx, dy, dz, [&](int n, TE cr, TE ci) {
-          if (valid && m <= p && n >= m) {
+        irregular_group<TE>(&tabs, p, dx, dy, dz, [&](int t2, int n, int m, bool v, TE vr, TE vi) {
+          if (valid && v) {
             const int kk = rl_re(n, m);
-            atomicAdd(&Lt[kk], to_double(f * cr));
-            if (m) atomicAdd(&Lt[kk + 1], to_double(-f * ci));
+            atomicAdd(&Lt[kk], to_double(f * vr));
+            if (m) atomicAdd(&Lt[kk + 1], to_double(-f * vi));
           }
         });
         if (prof_on && lane == 0) prof_item(rp.prof, 4, t_item);
@@ -624,14 +625,16 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
         }
       }
       if (!owner) continue;
-      // this half's contribution: the (at most one, nl >= 8) image of the
-      // target inside the half's interaction list.  The offset is known for
-      // the list the item came from (and for both halves when alpha =
-      // alpha' on this level); only the other half of a mixed item searches.
-      const int* cs = half ? cn : co;
+      // this side's contribution (group 0 old, group 1 new; groups 2, 3
+      // repeat them): the (at most one, nl >= 8) image of the target inside
+      // the side's interaction list.  The offset is known for the list the
+      // item came from (and for both sides when alpha = alpha' on this
+      // level); only the other side of a mixed item searches.
+      const int grp = lane >> 3, side = grp & 1;
+      const int* cs = side ? cn : co;
       int ofs[3] = {o_known[0], o_known[1], o_known[2]};
       bool have;
-      if (samel || (from_new && half == 1) || (!from_new && half == 0)) {
+      if (samel || (from_new && side == 1) || (!from_new && side == 0)) {
         have = true;
       } else if (!from_new) {
         have = false;  // the target is not in IL(alpha') (else not owner)
@@ -650,37 +653,30 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
           }
         }
       }
-      const TE f = have ? from_double<TE>(half ? g.q : -g.q) : TE(0);
+      const TE f = have ? from_double<TE>(side ? g.q : -g.q) : TE(0);
       TE dx = TE(3), dy = TE(3), dz = TE(3);
       if (have) {
         if (sizeof(TE) == 8) {
-          dx = (TE)(s_off[half][l][0] - s_kw[l][ofs[0] + 3]);
-          dy = (TE)(s_off[half][l][1] - s_kw[l][ofs[1] + 3]);
-          dz = (TE)(s_off[half][l][2] - s_kw[l][ofs[2] + 3]);
+          dx = (TE)(s_off[side][l][0] - s_kw[l][ofs[0] + 3]);
+          dy = (TE)(s_off[side][l][1] - s_kw[l][ofs[1] + 3]);
+          dz = (TE)(s_off[side][l][2] - s_kw[l][ofs[2] + 3]);
         } else {
-          dx = from_double<TE>(s_off[half][l][0]) - s_kwe[l][ofs[0] + 3];
-          dy = from_double<TE>(s_off[half][l][1]) - s_kwe[l][ofs[1] + 3];
-          dz = from_double<TE>(s_off[half][l][2]) - s_kwe[l][ofs[2] + 3];
+          dx = from_double<TE>(s_off[side][l][0]) - s_kwe[l][ofs[0] + 3];
+          dy = from_double<TE>(s_off[side][l][1]) - s_kwe[l][ofs[1] + 3];
+          dz = from_double<TE>(s_off[side][l][2]) - s_kwe[l][ofs[2] + 3];
         }
       }
-      TE ar[MC_PMAX + 1], ai[MC_PMAX + 1];
-      irregular_columns<TE>(&tabs, p, m, dx, dy, dz, [&](int n, TE cr, TE ci) {
-        ar[n] = f * cr;
-        ai[n] = -f * ci;
-      });
       double* st = stage[warp];
-#pragma unroll
-      for (int n = 0; n <= MC_PMAX; n++) {
-        if (n <= p) {
-          const TE orr = __shfl_xor_sync(0xffffffffu, ar[n], 16);
-          const TE oii = __shfl_xor_sync(0xffffffffu, ai[n], 16);
-          if (half == 0 && m <= n) {
-            const int kk = rl_re(n, m);
-            st[kk] = to_double(ar[n] + orr);
-            if (m) st[kk + 1] = to_double(ai[n] + oii);
-          }
+      irregular_group<TE>(&tabs, p, dx, dy, dz, [&](int t2, int n, int m, bool v, TE vr, TE vi) {
+        const TE cr = f * vr, ci = -f * vi;
+        const TE orr = __shfl_xor_sync(0xffffffffu, cr, 8);
+        const TE oii = __shfl_xor_sync(0xffffffffu, ci, 8);
+        if (grp == 0 && v) {
+          const int kk = rl_re(n, m);
+          st[kk] = to_double(cr + orr);
+          if (m) st[kk + 1] = to_double(ci + oii);
         }
-      }
+      });
       __syncwarp();
       double* Lt = S.Lhat + (size_t)(S.lev_off[l] + (tc[0] * nl + tc[1]) * nl + tc[2]) * C;
       {

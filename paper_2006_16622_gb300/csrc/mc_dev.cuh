@@ -58,6 +58,14 @@ struct McSys {
   int* status;       // device status word (MC_OK or MC_ERR_*)
   long long* stats;  // [4] steps, accepted, borderline, spare
   double* result;    // [4] dE of a single proposal, ...
+  // pipelined chain (mc_pipe.cu): second H and dipole buffers, speculative
+  // coarse-level deltas (3 rotating buffers of nsmall cells x C), sync words
+  double* Hhat2;     // [C]
+  double* dipv2;     // [3]
+  double* dsmall;    // [3 * nsmall * C]
+  int ls_end;        // first level with more than 4 cells per axis (or L + 1)
+  int nsmall;        // cells of levels lmin .. ls_end-1 (the first cells of Lhat)
+  unsigned long long* sync;  // [16]: [l] read epoch of level l, [12] near items done
 };
 
 struct RunParams {
@@ -190,8 +198,10 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* ctr, unsigned l
     unsigned long long t0 = mc_globaltimer();
     int ok = 1;
     unsigned spins = 0;
+    // poll with relaxed loads (an acquire per poll would invalidate the SM's
+    // L1 for every warp on it); one acquire fence once the count is reached
     while (true) {
-      asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
+      asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
       if (v >= target) break;
       if ((++spins & 255u) == 0u) {
         if ((long long)(mc_globaltimer() - t0) > wait_ns) {
@@ -205,6 +215,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* ctr, unsigned l
         }
       }
     }
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
     s_ok = ok;
   }
   __syncthreads();
@@ -287,6 +298,121 @@ __device__ __forceinline__ void irregular_columns(const HarmTabs<T>* t, int p, i
   T ir = mc_rsqrt(r2);
   T ir2 = ir * ir;
   harm_columns<T>(t->iA, t->iB, p, m, x * ir2, y * ir2, z * ir2, ir2, ir, use);
+}
+
+// ----------------------------------------------------- grouped evaluation
+// One harmonic set per group of 8 lanes (4 sets per warp).  Lane g of a
+// group owns the columns m1 = g and m2 = p - g (when m2 > m1), so every lane
+// makes p + 2 values in p + 2 identical steps (the triangle n >= m is split
+// evenly).  The diagonal values X_m^m = prod_{k<=m} f_k (f_0 = start, f_k =
+// A_k (x + i y)) come from a log-depth product scan over the group; the
+// columns then run the two-term recurrence with 6 flops per step.
+// use(t, n, m, re, im) is called for t = 0..p+1 (t is a compile-time
+// constant after unrolling); the value is valid when `valid` is passed true.
+template <typename T>
+__device__ __forceinline__ void cmul(T ar, T ai, T br, T bi, T* cr, T* ci) {
+  *cr = ar * br - ai * bi;
+  *ci = ar * bi + ai * br;
+}
+
+template <typename T, typename F>
+__device__ __forceinline__ void harm_group(const T (*A)[16], const T (*B)[16], int p, T X, T Y,
+                                           T Z, T Q, T start, F&& use) {
+  const int g = threadIdx.x & 7;
+  // factors f_{2g}, f_{2g+1} (the diagonal entries of the tables are A_k)
+  const int k0 = 2 * g, k1 = 2 * g + 1;
+  const T a0 = A[k0][k0], a1 = A[k1][k1];
+  T f0r = (k0 == 0) ? start : X * a0, f0i = (k0 == 0) ? T(0) : Y * a0;
+  const T f1r = X * a1, f1i = Y * a1;
+  T Pr, Pi;
+  cmul(f0r, f0i, f1r, f1i, &Pr, &Pi);
+  // inclusive product scan of P over the 8 lanes of the group
+  T Ir = Pr, Ii = Pi;
+#pragma unroll
+  for (int d = 1; d < 8; d <<= 1) {
+    const T ur = __shfl_up_sync(0xffffffffu, Ir, d, 8), ui = __shfl_up_sync(0xffffffffu, Ii, d, 8);
+    if (g >= d) {
+      T nr, ni;
+      cmul(ur, ui, Ir, Ii, &nr, &ni);
+      Ir = nr;
+      Ii = ni;
+    }
+  }
+  T Er = __shfl_up_sync(0xffffffffu, Ir, 1, 8), Ei = __shfl_up_sync(0xffffffffu, Ii, 1, 8);
+  if (g == 0) {
+    Er = T(1);
+    Ei = T(0);
+  }
+  T D0r, D0i;  // X_{2g}^{2g}
+  cmul(Er, Ei, f0r, f0i, &D0r, &D0i);
+  const T D1r = Ir, D1i = Ii;  // X_{2g+1}^{2g+1}
+  const int m1 = g, m2 = p - g;
+  const bool active = m1 <= m2;
+  const bool two = m2 > m1;
+  // fetch X_m^m for m = m1, m2 from lane m/2 of the group
+  const T e1r = __shfl_sync(0xffffffffu, D0r, m1 >> 1, 8), e1i = __shfl_sync(0xffffffffu, D0i, m1 >> 1, 8);
+  const T o1r = __shfl_sync(0xffffffffu, D1r, m1 >> 1, 8), o1i = __shfl_sync(0xffffffffu, D1i, m1 >> 1, 8);
+  const int m2c = (m2 >= 0 && m2 <= 15) ? m2 : 0;
+  const T e2r = __shfl_sync(0xffffffffu, D0r, m2c >> 1, 8), e2i = __shfl_sync(0xffffffffu, D0i, m2c >> 1, 8);
+  const T o2r = __shfl_sync(0xffffffffu, D1r, m2c >> 1, 8), o2i = __shfl_sync(0xffffffffu, D1i, m2c >> 1, 8);
+  const T d1r = (m1 & 1) ? o1r : e1r, d1i = (m1 & 1) ? o1i : e1i;
+  const T d2r = (m2c & 1) ? o2r : e2r, d2i = (m2c & 1) ? o2i : e2i;
+  const int len1 = p - m1 + 1;
+  T p1r = T(0), p1i = T(0), p2r = T(0), p2i = T(0);
+#pragma unroll
+  for (int t = 0; t <= MC_PMAX + 1; t++) {
+    if (t <= p + 1) {
+      const bool c1 = t < len1;
+      const int m = c1 ? m1 : m2c;
+      const int n = c1 ? (m1 + t) : (m2c + t - len1);
+      const bool valid = active && (c1 || two) && n <= p;
+      const bool st = (n == m);
+      const int nn = n > 15 ? 15 : n;
+      const T a = Z * A[nn][m], b = Q * B[nn][m];
+      T vr = a * p1r - b * p2r, vi = a * p1i - b * p2i;
+      const T sr = c1 ? d1r : d2r, si = c1 ? d1i : d2i;
+      vr = st ? sr : vr;
+      vi = st ? si : vi;
+      p2r = st ? T(0) : p1r;
+      p2i = st ? T(0) : p1i;
+      p1r = vr;
+      p1i = vi;
+      use(t, n, m, valid, vr, vi);
+    }
+  }
+}
+
+// (n, m) of step t of this lane in harm_group, for preloading coefficients
+__device__ __forceinline__ void group_nm(int p, int t, int* n, int* m, bool* valid) {
+  const int g = threadIdx.x & 7;
+  const int m1 = g, m2 = p - g;
+  const int m2c = (m2 >= 0 && m2 <= 15) ? m2 : 0;
+  const int len1 = p - m1 + 1;
+  const bool c1 = t < len1;
+  *m = c1 ? m1 : m2c;
+  *n = c1 ? (m1 + t) : (m2c + t - len1);
+  *valid = (m1 <= m2) && (c1 || m2 > m1) && *n <= p;
+}
+
+template <typename T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T, typename F>
+__device__ __forceinline__ void regular_group(const HarmTabs<T>* t, int p, T x, T y, T z, F&& use) {
+  const T r2 = x * x + y * y + z * z;
+  harm_group<T>(t->rA, t->rB, p, x, y, z, r2, T(1), use);
+}
+
+template <typename T, typename F>
+__device__ __forceinline__ void irregular_group(const HarmTabs<T>* t, int p, T x, T y, T z, F&& use) {
+  const T r2 = x * x + y * y + z * z;
+  const T ir = mc_rsqrt(r2);
+  const T ir2 = ir * ir;
+  harm_group<T>(t->iA, t->iB, p, x * ir2, y * ir2, z * ir2, ir2, ir, use);
 }
 
 // index of (n, m) in the real layout (re part; im part is +1 for m > 0)

@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(MC_THREADS)
   harm_tabs_init<double>(&tabs);
   il_table_init(il);
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane >> 4, m = lane & 15;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane >> 3;
   const int p = S.p, C = S.C, L = S.L;
   const bool pbc = S.bc == 0;
   const int nl = S.lev_n[l], f = 1 << (L - l), nL = S.nL;
@@ -96,9 +96,9 @@ __global__ void __launch_bounds__(MC_THREADS)
     const int tc[3] = {t / (nl * nl), (t / nl) % nl, t % nl};
     const int par = ((tc[0] & 1) << 2) | ((tc[1] & 1) << 1) | (tc[2] & 1);
     const double Rt[3] = {(tc[0] + 0.5) * w, (tc[1] + 0.5) * w, (tc[2] + 0.5) * w};
-    double ar[MC_PMAX + 1], ai[MC_PMAX + 1];
+    double ar[MC_PMAX + 2], ai[MC_PMAX + 2];
 #pragma unroll
-    for (int n = 0; n <= MC_PMAX; n++) ar[n] = ai[n] = 0.0;
+    for (int q = 0; q <= MC_PMAX + 1; q++) ar[q] = ai[q] = 0.0;
     const int kb = ch * per, ke = min(189, kb + per);
     for (int k = kb; k < ke; k++) {
       int ox, oy, oz;
@@ -117,37 +117,45 @@ __global__ void __launch_bounds__(MC_THREADS)
         shift[d] = (double)((e[d] - src[d]) / nl) * S.a;
       }
       if (!ok) continue;
-      // the finest cells inside the source cell
+      const double bx = shift[0] - Rt[0], by = shift[1] - Rt[1], bz = shift[2] - Rt[2];
+      // the finest cells inside the source cell; four charges per step
       for (int fc = 0; fc < f * f * f; fc++) {
         const int gx = src[0] * f + fc / (f * f), gy = src[1] * f + (fc / f) % f,
                   gz = src[2] * f + fc % f;
         const int cell = (gx * nL + gy) * nL + gz;
         const int cnt = S.ccount[cell];
-        for (int s0 = 0; s0 < cnt; s0 += 2) {
-          const int s = s0 + half;
+        for (int s0 = 0; s0 < cnt; s0 += 4) {
+          const int s = s0 + grp;
           const bool act = s < cnt;
           double4 v = make_double4(0, 0, 0, 0);
           if (act) v = S.cpos[(size_t)cell * S.cap + s];
-          const double dx = act ? v.x + shift[0] - Rt[0] : 3.0;
-          const double dy = act ? v.y + shift[1] - Rt[1] : 3.0;
-          const double dz = act ? v.z + shift[2] - Rt[2] : 3.0;
+          const double dx = act ? v.x + bx : 3.0;
+          const double dy = act ? v.y + by : 3.0;
+          const double dz = act ? v.z + bz : 3.0;
           const double qi = act ? v.w : 0.0;
-          irregular_columns<double>(&tabs, p, m, dx, dy, dz, [&](int n, double cr, double ci) {
-            ar[n] += qi * cr;
-            ai[n] -= qi * ci;
-          });
+          irregular_group<double>(&tabs, p, dx, dy, dz,
+                                  [&](int t2, int n, int m, bool vld, double cr, double ci) {
+                                    ar[t2] += qi * cr;
+                                    ai[t2] -= qi * ci;
+                                  });
         }
       }
     }
     double* st = stage[warp];
 #pragma unroll
-    for (int n = 0; n <= MC_PMAX; n++) {
-      const double orr = __shfl_xor_sync(0xffffffffu, ar[n], 16);
-      const double oii = __shfl_xor_sync(0xffffffffu, ai[n], 16);
-      if (half == 0 && n <= p && m <= n) {
+    for (int t2 = 0; t2 <= MC_PMAX + 1; t2++) {
+      double vr = ar[t2], vi = ai[t2];
+      vr += __shfl_xor_sync(0xffffffffu, vr, 8);
+      vi += __shfl_xor_sync(0xffffffffu, vi, 8);
+      vr += __shfl_xor_sync(0xffffffffu, vr, 16);
+      vi += __shfl_xor_sync(0xffffffffu, vi, 16);
+      int n, m;
+      bool vld;
+      group_nm(p, t2, &n, &m, &vld);
+      if (grp == 0 && vld) {
         const int kk = rl_re(n, m);
-        st[kk] = ar[n] + orr;
-        if (m) st[kk + 1] = ai[n] + oii;
+        st[kk] = vr;
+        if (m) st[kk + 1] = vi;
       }
     }
     __syncwarp();
@@ -181,27 +189,27 @@ __global__ void __launch_bounds__(MC_THREADS)
   if (threadIdx.x == 0) S = *sysp;
   harm_tabs_init<double>(&tabs);
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane >> 4, m = lane & 15;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane >> 3, g8 = lane & 7;
   const int p = S.p, C = S.C;
   const int per = (S.n + nchunk - 1) / nchunk;
   const double c1 = 0.5 * S.a;
   for (int ch = blockIdx.x * MC_WARPS + warp; ch < nchunk; ch += gridDim.x * MC_WARPS) {
-    double ar[MC_PMAX + 1], ai[MC_PMAX + 1];
+    double ar[MC_PMAX + 2], ai[MC_PMAX + 2];
 #pragma unroll
-    for (int n = 0; n <= MC_PMAX; n++) ar[n] = ai[n] = 0.0;
+    for (int q = 0; q <= MC_PMAX + 1; q++) ar[q] = ai[q] = 0.0;
     double D[3] = {0, 0, 0};
     const int ib = ch * per, ie = min(S.n, ib + per);
-    for (int i0 = ib; i0 < ie; i0 += 2) {
-      const int i = i0 + half;
+    for (int i0 = ib; i0 < ie; i0 += 4) {
+      const int i = i0 + grp;
       const bool act = i < ie;
       double4 v = make_double4(c1, c1, c1, 0.0);
       if (act) v = S.ppos[i];
-      regular_columns<double>(&tabs, p, m, v.x - c1, v.y - c1, v.z - c1,
-                              [&](int n, double cr, double ci) {
-                                ar[n] += v.w * cr;
-                                ai[n] -= v.w * ci;
-                              });
-      if (m == 0) {
+      regular_group<double>(&tabs, p, v.x - c1, v.y - c1, v.z - c1,
+                            [&](int t2, int n, int m, bool vld, double cr, double ci) {
+                              ar[t2] += v.w * cr;
+                              ai[t2] -= v.w * ci;
+                            });
+      if (g8 == 0) {
         D[0] += v.w * v.x;
         D[1] += v.w * v.y;
         D[2] += v.w * v.z;
@@ -209,16 +217,25 @@ __global__ void __launch_bounds__(MC_THREADS)
     }
     double* st = stage[warp];
 #pragma unroll
-    for (int n = 0; n <= MC_PMAX; n++) {
-      const double orr = __shfl_xor_sync(0xffffffffu, ar[n], 16);
-      const double oii = __shfl_xor_sync(0xffffffffu, ai[n], 16);
-      if (half == 0 && n <= p && m <= n) {
+    for (int t2 = 0; t2 <= MC_PMAX + 1; t2++) {
+      double vr = ar[t2], vi = ai[t2];
+      vr += __shfl_xor_sync(0xffffffffu, vr, 8);
+      vi += __shfl_xor_sync(0xffffffffu, vi, 8);
+      vr += __shfl_xor_sync(0xffffffffu, vr, 16);
+      vi += __shfl_xor_sync(0xffffffffu, vi, 16);
+      int n, m;
+      bool vld;
+      group_nm(p, t2, &n, &m, &vld);
+      if (grp == 0 && vld) {
         const int kk = rl_re(n, m);
-        st[kk] = ar[n] + orr;
-        if (m) st[kk + 1] = ai[n] + oii;
+        st[kk] = vr;
+        if (m) st[kk + 1] = vi;
       }
     }
-    for (int d = 0; d < 3; d++) D[d] += __shfl_xor_sync(0xffffffffu, D[d], 16);
+    for (int d = 0; d < 3; d++) {
+      D[d] += __shfl_xor_sync(0xffffffffu, D[d], 8);
+      D[d] += __shfl_xor_sync(0xffffffffu, D[d], 16);
+    }
     __syncwarp();
     double* o = out + (size_t)ch * (C + 3);
     for (int kk = lane; kk < C; kk += 32) o[kk] = st[kk];
@@ -265,7 +282,7 @@ __global__ void __launch_bounds__(MC_THREADS)
   if (threadIdx.x == 0) S = *sysp;
   harm_tabs_init<double>(&tabs);
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane >> 4, m = lane & 15;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int p = S.p, C = S.C, L = S.L, nL = S.nL;
   const bool pbc = S.bc == 0;
   const int gw = blockIdx.x * MC_WARPS + warp, nw = gridDim.x * MC_WARPS;
@@ -275,33 +292,34 @@ __global__ void __launch_bounds__(MC_THREADS)
     const int cf[3] = {finest_coord(v.x, S.inv_wL, nL), finest_coord(v.y, S.inv_wL, nL),
                        finest_coord(v.z, S.inv_wL, nL)};
     double phi = 0.0;
-    // level expansions: two levels per warp step (one per half-warp)
+    // level expansions: four levels per warp step (one per 8-lane group)
     const int nlev = L - S.lmin + 1;
-    for (int l0 = 0; l0 < nlev; l0 += 2) {
-      const int li = l0 + half;
+    const int grp = lane >> 3;
+    for (int l0 = 0; l0 < nlev; l0 += 4) {
+      const int li = l0 + grp;
       const bool act = li < nlev;
       const int l = act ? L - li : L;
       const int sh = L - l, nl = S.lev_n[l];
       const double w = S.lev_w[l];
       const int cx = cf[0] >> sh, cy = cf[1] >> sh, cz = cf[2] >> sh;
       const double* Lb = S.Lhat + (size_t)(S.lev_off[l] + (cx * nl + cy) * nl + cz) * C;
-      double Lr[MC_PMAX + 1], Li[MC_PMAX + 1];
+      double Lr[MC_PMAX + 2], Li[MC_PMAX + 2];
 #pragma unroll
-      for (int n = 0; n <= MC_PMAX; n++) {
-        Lr[n] = Li[n] = 0.0;
-        if (act && n <= p && m <= n) {
-          const int k = rl_re(n, m);
-          Lr[n] = Lb[k];
-          if (m) Li[n] = Lb[k + 1];
-        }
+      for (int t2 = 0; t2 <= MC_PMAX + 1; t2++) {
+        int n, m;
+        bool vld;
+        group_nm(p, t2, &n, &m, &vld);
+        const int k = rl_re(n, m);
+        Lr[t2] = (act && vld) ? Lb[k] : 0.0;
+        Li[t2] = (act && vld && m) ? Lb[k + 1] : 0.0;
       }
       double acc = 0.0;
-      regular_columns<double>(&tabs, p, m, v.x - (cx + 0.5) * w, v.y - (cy + 0.5) * w,
-                              v.z - (cz + 0.5) * w, [&](int n, double cr, double ci) {
-                                if (n >= m) acc += Lr[n] * cr - Li[n] * ci;
-                              });
-      if (m > p || !act) acc = 0.0;
-      if (m > 0) acc *= 2.0;
+      regular_group<double>(&tabs, p, v.x - (cx + 0.5) * w, v.y - (cy + 0.5) * w,
+                            v.z - (cz + 0.5) * w,
+                            [&](int t2, int n, int m, bool vld, double cr, double ci) {
+                              if (vld) acc += (m ? 2.0 : 1.0) * (Lr[t2] * cr - Li[t2] * ci);
+                            });
+      if (!act) acc = 0.0;
       phi += acc;
     }
     // direct near cells

@@ -18,13 +18,15 @@ MC_OK = 0
 BC_PBC, BC_FREE = 0, 1
 TINFOIL, VACUUM = 0, 1
 FP64, FP32_EVAL = 0, 1
+SCHEDULE_PHASED, SCHEDULE_PIPELINED = 0, 1
 SETUP_P2L = 0
 
 EXPORTED = ["mc_init", "mc_setup", "mc_propose", "mc_accept", "mc_run", "mc_energy",
             "mc_energy_fresh", "mc_get_positions", "mc_get_local", "mc_get_far",
             "mc_lattice_sums", "mc_status", "mc_set_wait_limit", "mc_profile", "mc_profile_read",
             "mc_destroy", "mc_strerror", "mc_p2l_level_noalloc", "mc_batch_create",
-            "mc_batch_tune", "mc_batch_run", "mc_batch_info", "mc_batch_destroy"]
+            "mc_batch_tune", "mc_batch_run", "mc_batch_info", "mc_batch_destroy",
+            "mc_set_schedule", "mc_batch_set_schedule"]
 
 
 class McStats(ctypes.Structure):
@@ -73,6 +75,8 @@ def load(path: str = LIB_PATH):
     L.mc_batch_tune.argtypes = [P, I64, D, D]
     L.mc_batch_run.argtypes = [P, I64, P, D, D, P, P, P, P]
     L.mc_batch_info.argtypes = [P, P, P]
+    L.mc_set_schedule.argtypes = [P, I]
+    L.mc_batch_set_schedule.argtypes = [P, I]
     L.mc_batch_destroy.argtypes = [P]
     L.mc_batch_destroy.restype = None
     L.mc_strerror.argtypes = [I]
@@ -208,6 +212,9 @@ class Context:
         _check(load().mc_profile_read(self._h, _ptr(out)), "mc_profile_read")
         return out
 
+    def set_schedule(self, schedule):
+        _check(load().mc_set_schedule(self._h, int(schedule)), "mc_set_schedule")
+
     def set_wait_limit(self, ns):
         _check(load().mc_set_wait_limit(self._h, int(ns)), "mc_set_wait_limit")
 
@@ -239,6 +246,9 @@ class Batch:
     def tune(self, trial_steps=500, beta=1.0, half_width=0.3):
         _check(load().mc_batch_tune(self._h, int(trial_steps), float(beta), float(half_width)),
                "mc_batch_tune")
+
+    def set_schedule(self, schedule):
+        _check(load().mc_batch_set_schedule(self._h, int(schedule)), "mc_batch_set_schedule")
 
     def info(self):
         ctas = np.zeros(len(self.contexts), dtype=np.int32)

@@ -38,8 +38,9 @@ def _lib():
     mcfmm.load()
 
 
-@pytest.mark.parametrize("precision", [mcfmm.FP64])
-def test_batch_replays_every_chain(precision):
+@pytest.mark.parametrize("precision,schedule", [(mcfmm.FP64, mcfmm.SCHEDULE_PHASED),
+                                                (mcfmm.FP64, mcfmm.SCHEDULE_PIPELINED)])
+def test_batch_replays_every_chain(precision, schedule):
     syst = _systems()
     ctxs = []
     for pos, q, a, L in syst:
@@ -47,6 +48,7 @@ def test_batch_replays_every_chain(precision):
         c.setup()
         ctxs.append(c)
     b = mcfmm.Batch(ctxs)
+    b.set_schedule(schedule)
     seeds = np.arange(len(ctxs), dtype=np.uint64) + 7
     steps = 400
     r = b.run(steps, seeds, beta=1.0, half_width=0.4, log=True)

@@ -93,10 +93,12 @@ def test_propose_accept_sequence(bc):
     assert _rel(g.energy(), o.energy()) <= DE_TOL
 
 
-def test_replay_small_workload_full_chain():
+@pytest.mark.parametrize("schedule", [mcfmm.SCHEDULE_PHASED, mcfmm.SCHEDULE_PIPELINED])
+def test_replay_small_workload_full_chain(schedule):
     """N=1000, a=10, L=3, p=8, h=0.5, beta=1, seed 0: the full 10^4-move chain"""
     n, a, L, p = 1000, 10.0, 3, 8
     g, o, pos, q = _pair(n, a, L, p, seed=0)
+    g.set_schedule(schedule)
     steps = 10_000
     rg = g.run(steps, seed=0, beta=1.0, half_width=0.5, log=True)
     ro = o.run(steps, seed=0, step0=0, beta=1.0, half_width=0.5)
@@ -110,10 +112,12 @@ def test_replay_small_workload_full_chain():
     assert np.array_equal(g.positions(), o.positions())
 
 
-def test_replay_ragged_and_edge_cases():
+@pytest.mark.parametrize("schedule", [mcfmm.SCHEDULE_PHASED, mcfmm.SCHEDULE_PIPELINED])
+def test_replay_ragged_and_edge_cases(schedule):
     # tiny box with 2 cells per axis (27 image copies of every cell), p = 0
-    for (n, a, L, p) in [(16, 3.0, 2, 0), (40, 5.0, 2, 3), (126, 7.0, 3, 5)]:
+    for (n, a, L, p) in [(16, 3.0, 2, 0), (40, 5.0, 2, 3), (126, 7.0, 3, 5), (900, 9.0, 4, 7)]:
         g, o, pos, q = _pair(n, a, L, p, seed=n)
+        g.set_schedule(schedule)
         rg = g.run(500, seed=9, beta=0.7, half_width=0.9, log=True)
         ro = o.run(500, seed=9, step0=0, beta=0.7, half_width=0.9)
         assert np.array_equal(rg["acc"], ro["acc"])
