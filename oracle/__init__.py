@@ -61,6 +61,7 @@ def lib():
                                      ctypes.c_int, ctypes.c_int]
             L.orc_destroy.argtypes = [_P]
             L.orc_setup.argtypes = [_P]
+            L.orc_setup_fmm.argtypes = [_P]
             L.orc_propose.restype = _D
             L.orc_propose.argtypes = [_P, _I64, _P]
             L.orc_last_parts.argtypes = [_P, _P]
@@ -211,6 +212,9 @@ class System:
 
     def setup(self):
         lib().orc_setup(self._h)
+
+    def setup_fmm(self):
+        lib().orc_setup_fmm(self._h)
 
     def propose(self, j, rnew):
         r = _f64(rnew)

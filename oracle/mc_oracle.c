@@ -378,6 +378,7 @@ struct orc_sys {
 };
 
 static int ncell_axis(int l) { return 1 << (l - 1); }
+static void setup_KE(orc_sys *s);
 static double cell_width(const orc_sys *s, int l) { return s->a / (double)ncell_axis(l); }
 
 /* finest-level cell coordinates: floor(x * nL / a), clamped to nL-1; a
@@ -604,6 +605,65 @@ static void setup_local(orc_sys *s) {
       }
     }
   }
+}
+
+/* ---- FMM-variant initialisation (Sec. 3.2, last paragraph): multipole
+ * expansions (Eq. 4) of every cell, then for every cell its local expansion
+ * Psi^Delta as the sum of the multipole-to-local translations of the cells
+ * of its interaction list (no local-to-local accumulation: the per-level
+ * expansions are kept separate).  Multipoles are taken directly from the
+ * particles on each level (the truncated upward translation is exact, so this
+ * is the same multipole set). ---- */
+static void setup_local_fmm(orc_sys *s) {
+  int C = s->C, p = s->p, C2 = (2 * p + 1) * (2 * p + 1);
+  int off[189][3];
+  cplx *G = (cplx *)malloc(sizeof(cplx) * C2);
+  cplx *R = (cplx *)malloc(sizeof(cplx) * C);
+  cplx *T = (cplx *)malloc(sizeof(cplx) * C);
+  for (int l = 2; l <= s->L; l++) {
+    int nl = ncell_axis(l);
+    size_t ncell = (size_t)nl * nl * nl;
+    double w = cell_width(s, l);
+    cplx *M = (cplx *)calloc(ncell * C, sizeof(cplx));
+    /* Eq. (4) about each cell centre */
+    for (int64_t i = 0; i < s->n; i++) {
+      int cf[3], c[3];
+      finest_cell(s, &s->pos[3 * i], cf);
+      for (int d = 0; d < 3; d++) c[d] = cf[d] >> (s->L - l);
+      double Rc[3], d3[3];
+      cell_centre(s, l, c, Rc);
+      for (int t = 0; t < 3; t++) d3[t] = s->pos[3 * i + t] - Rc[t];
+      regular_table(p, d3, R);
+      cplx *Mc = M + (size_t)lin(nl, c) * C;
+      for (int nn = 0; nn <= p; nn++)
+        for (int m = -nn; m <= nn; m++) Mc[IDX(nn, m)] += s->q[i] * R[IDX(nn, -m)];
+    }
+    memset(s->Lx[l], 0, sizeof(cplx) * ncell * C);
+    for (size_t b = 0; b < ncell; b++) {
+      int bc[3] = {(int)(b / ((size_t)nl * nl)), (int)((b / nl) % nl), (int)(b % nl)};
+      int nIL = il_offsets(bc, off);
+      cplx *Lb = s->Lx[l] + b * C;
+      for (int k = 0; k < nIL; k++) {
+        int e[3] = {bc[0] + off[k][0], bc[1] + off[k][1], bc[2] + off[k][2]}, cc[3], sh[3];
+        if (!wrap_cell(s, nl, e, cc, sh)) continue;
+        /* source multipole centre relative to the target centre */
+        double cvec[3] = {off[k][0] * w, off[k][1] * w, off[k][2] * w};
+        irregular_table(2 * p, cvec, G);
+        m2l_apply(p, M + (size_t)lin(nl, cc) * C, G, T);
+        for (int q = 0; q < C; q++) Lb[q] += T[q];
+      }
+    }
+    free(M);
+  }
+  free(G);
+  free(R);
+  free(T);
+}
+
+void orc_setup_fmm(orc_sys *s) {
+  setup_local_fmm(s);
+  if (s->bc == ORC_BC_PBC) setup_KE(s);
+  s->energy = orc_energy_fresh(s);
 }
 
 /* ---- Sec. 3.3 (ii): K_n^m = sum q r^n Y_n^-m, E_n^m = sum q r^n Y_n^m ---- */

@@ -53,6 +53,8 @@ orc_sys *orc_create(int64_t n, const double *pos, const double *q, double a,
                     int levels, int p, int bc, int dipole_bc);
 void orc_destroy(orc_sys *s);
 void orc_setup(orc_sys *s);                       /* Alg. L.3 + K/E + U0 */
+/* FMM-variant initialisation: per-level multipoles + M2L over interaction lists */
+void orc_setup_fmm(orc_sys *s);
 double orc_propose(orc_sys *s, int64_t j, const double rnew[3]);  /* Alg. L.1 */
 /* split of the last proposal: [0] expansions, [1] direct (Alg. 1 incl.
  * image correction), [2] far lattice, [3] dipole (tinfoil) term */

@@ -384,3 +384,31 @@ def test_proposal_stream_statistics():
     b = O.philox([1, 0, 1, 0], [7, 0])
     c = O.philox([1, 0, 0, 0], [8, 0])
     assert not np.array_equal(a, b) and not np.array_equal(a, c)
+
+
+def test_fmm_variant_setup_converges_to_exact_setup_and_direct_sums():
+    """The FMM-variant setup (Sec. 3.2: per-level multipoles translated into
+    each cell's interaction list) equals Alg. L.3 up to the multipole
+    truncation, so its distance to the P2L setup falls with p; in free space
+    its energy converges to the direct pair sum."""
+    pos, q = uniform_system(200, 6.0, seed=21)
+    gaps = []
+    for p in (4, 6, 8):
+        a = O.System(pos, q, 6.0, 3, p)
+        a.setup()
+        b = O.System(pos, q, 6.0, 3, p)
+        b.setup_fmm()
+        gaps.append(max(np.max(np.abs(a.local(l) - b.local(l))) / np.max(np.abs(a.local(l)))
+                        for l in (2, 3)))
+        Ka, _ = a.KH()
+        Kb, _ = b.KH()
+        assert np.max(np.abs(Ka - Kb)) <= 1e-12 * np.max(np.abs(Ka))
+    assert gaps[0] > 3 * gaps[1] > 9 * gaps[2] and gaps[2] < 5e-5
+    pos, q = uniform_system(200, 8.0, seed=22)
+    Ud = O.direct_energy(pos, q)
+    errs = []
+    for p in (4, 8, 12):
+        b = O.System(pos, q, 8.0, 3, p, bc=O.BC_FREE)
+        b.setup_fmm()
+        errs.append(abs(b.energy() - Ud) / abs(Ud))
+    assert errs[0] > 10 * errs[1] > 100 * errs[2] and errs[2] < 1e-6
