@@ -49,6 +49,10 @@ extern "C" {
 #define MC_FP32_EVAL 1 /* harmonics and near field in FP32; FP64 accumulators,
                           energy and periodic lattice term */
 #define MC_SETUP_P2L 0 /* Alg. L.3 as a per-target gather */
+#define MC_SETUP_FMM 1 /* FMM variant (Sec. 3.2, last paragraph): per-level
+                          multipoles, then multipole-to-local over the
+                          interaction lists; equal to MC_SETUP_P2L up to the
+                          multipole truncation */
 
 typedef struct mc_ctx mc_ctx;
 
@@ -77,7 +81,9 @@ int mc_init(mc_ctx **out, int64_t n, const double *pos, const double *q, double 
 
 /* Alg. L.3 (initialise local expansions), the box multipole K/E of
  * Sec. 3.3 (ii), the lattice local expansion H = R(K) and the total energy.
- * mode: MC_SETUP_P2L.  Synchronous. */
+ * mode: MC_SETUP_P2L (exact P2L of every charge) or MC_SETUP_FMM (the
+ * O(p^4 N) FMM variant; allocates its multipole and offset tables on first
+ * use).  Synchronous. */
 int mc_setup(mc_ctx *ctx, int mode);
 
 /* Alg. L.1 with Alg. 1 and the periodic terms of Sec. 3.3: the energy change

@@ -62,6 +62,7 @@ def lib():
             L.orc_destroy.argtypes = [_P]
             L.orc_setup.argtypes = [_P]
             L.orc_setup_fmm.argtypes = [_P]
+            L.orc_fmm_local_cell.argtypes = [_P, ctypes.c_int, _P, _P]
             L.orc_propose.restype = _D
             L.orc_propose.argtypes = [_P, _I64, _P]
             L.orc_last_parts.argtypes = [_P, _P]
@@ -215,6 +216,13 @@ class System:
 
     def setup_fmm(self):
         lib().orc_setup_fmm(self._h)
+
+    def fmm_local_cell(self, level, c):
+        cc = np.ascontiguousarray(np.asarray(c, dtype=np.int32))
+        out = np.zeros(self.C)
+        if lib().orc_fmm_local_cell(self._h, level, _ptr(cc), _ptr(out)) != 0:
+            raise ValueError("bad level")
+        return out
 
     def propose(self, j, rnew):
         r = _f64(rnew)

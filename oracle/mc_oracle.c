@@ -379,6 +379,7 @@ struct orc_sys {
 
 static int ncell_axis(int l) { return 1 << (l - 1); }
 static void setup_KE(orc_sys *s);
+static void to_real_layout(int p, const cplx *X, double *out);
 static double cell_width(const orc_sys *s, int l) { return s->a / (double)ncell_axis(l); }
 
 /* finest-level cell coordinates: floor(x * nL / a), clamped to nL-1; a
@@ -514,7 +515,7 @@ orc_sys *orc_create(int64_t n, const double *pos, const double *q, double a, int
     for (int k = 0; k < (lmax + 1) * (lmax + 1); k++) s->Slat[k] = tmp[2 * k] + I * tmp[2 * k + 1];
     free(tmp);
   }
-  if (bc == ORC_BC_PBC) {
+  {
     s->m2lf = (double *)malloc(sizeof(double) * s->C * s->C);
     for (int j = 0; j <= p; j++)
       for (int k = -j; k <= j; k++)
@@ -614,16 +615,70 @@ static void setup_local(orc_sys *s) {
  * expansions are kept separate).  Multipoles are taken directly from the
  * particles on each level (the truncated upward translation is exact, so this
  * is the same multipole set). ---- */
-static void setup_local_fmm(orc_sys *s) {
+/* sum over the interaction list of one target cell bc of level l of the
+ * multipole-to-local translations; Mlev holds the level's multipoles, or is
+ * NULL to take each source multipole directly from the particles */
+static void fmm_target(orc_sys *s, int l, const int bc[3], const cplx *Mlev, cplx *Lb) {
   int C = s->C, p = s->p, C2 = (2 * p + 1) * (2 * p + 1);
+  int nl = ncell_axis(l);
+  double w = cell_width(s, l);
   int off[189][3];
   cplx *G = (cplx *)malloc(sizeof(cplx) * C2);
-  cplx *R = (cplx *)malloc(sizeof(cplx) * C);
   cplx *T = (cplx *)malloc(sizeof(cplx) * C);
+  cplx *Ms = (cplx *)malloc(sizeof(cplx) * C);
+  cplx *R = (cplx *)malloc(sizeof(cplx) * C);
+  memset(Lb, 0, sizeof(cplx) * C);
+  int nIL = il_offsets(bc, off);
+  for (int k = 0; k < nIL; k++) {
+    int e[3] = {bc[0] + off[k][0], bc[1] + off[k][1], bc[2] + off[k][2]}, cc[3], sh[3];
+    if (!wrap_cell(s, nl, e, cc, sh)) continue;
+    const cplx *M;
+    if (Mlev) {
+      M = Mlev + (size_t)lin(nl, cc) * C;
+    } else {
+      /* Eq. (4) about the source cell's centre, from its charges */
+      memset(Ms, 0, sizeof(cplx) * C);
+      double Rc[3], d3[3];
+      cell_centre(s, l, cc, Rc);
+      for (int64_t i = 0; i < s->n; i++) {
+        int cf[3];
+        finest_cell(s, &s->pos[3 * i], cf);
+        if ((cf[0] >> (s->L - l)) != cc[0] || (cf[1] >> (s->L - l)) != cc[1] ||
+            (cf[2] >> (s->L - l)) != cc[2])
+          continue;
+        for (int t = 0; t < 3; t++) d3[t] = s->pos[3 * i + t] - Rc[t];
+        regular_table(p, d3, R);
+        for (int nn = 0; nn <= p; nn++)
+          for (int m = -nn; m <= nn; m++) Ms[IDX(nn, m)] += s->q[i] * R[IDX(nn, -m)];
+      }
+      M = Ms;
+    }
+    /* source multipole centre relative to the target centre */
+    double cvec[3] = {off[k][0] * w, off[k][1] * w, off[k][2] * w};
+    irregular_table(2 * p, cvec, G);
+    /* m2l_apply with the translation factors tabulated */
+    for (int j = 0; j <= p; j++)
+      for (int kk = -j; kk <= j; kk++) {
+        const double *f = s->m2lf + (size_t)IDX(j, kk) * C;
+        cplx acc = 0.0;
+        for (int n = 0; n <= p; n++)
+          for (int m = -n; m <= n; m++) acc += M[IDX(n, m)] * f[IDX(n, m)] * G[IDX(j + n, m - kk)];
+        T[IDX(j, kk)] = acc;
+      }
+    for (int q = 0; q < C; q++) Lb[q] += T[q];
+  }
+  free(G);
+  free(T);
+  free(Ms);
+  free(R);
+}
+
+static void setup_local_fmm(orc_sys *s) {
+  int C = s->C, p = s->p;
+  cplx *R = (cplx *)malloc(sizeof(cplx) * C);
   for (int l = 2; l <= s->L; l++) {
     int nl = ncell_axis(l);
     size_t ncell = (size_t)nl * nl * nl;
-    double w = cell_width(s, l);
     cplx *M = (cplx *)calloc(ncell * C, sizeof(cplx));
     /* Eq. (4) about each cell centre */
     for (int64_t i = 0; i < s->n; i++) {
@@ -638,26 +693,24 @@ static void setup_local_fmm(orc_sys *s) {
       for (int nn = 0; nn <= p; nn++)
         for (int m = -nn; m <= nn; m++) Mc[IDX(nn, m)] += s->q[i] * R[IDX(nn, -m)];
     }
-    memset(s->Lx[l], 0, sizeof(cplx) * ncell * C);
     for (size_t b = 0; b < ncell; b++) {
       int bc[3] = {(int)(b / ((size_t)nl * nl)), (int)((b / nl) % nl), (int)(b % nl)};
-      int nIL = il_offsets(bc, off);
-      cplx *Lb = s->Lx[l] + b * C;
-      for (int k = 0; k < nIL; k++) {
-        int e[3] = {bc[0] + off[k][0], bc[1] + off[k][1], bc[2] + off[k][2]}, cc[3], sh[3];
-        if (!wrap_cell(s, nl, e, cc, sh)) continue;
-        /* source multipole centre relative to the target centre */
-        double cvec[3] = {off[k][0] * w, off[k][1] * w, off[k][2] * w};
-        irregular_table(2 * p, cvec, G);
-        m2l_apply(p, M + (size_t)lin(nl, cc) * C, G, T);
-        for (int q = 0; q < C; q++) Lb[q] += T[q];
-      }
+      fmm_target(s, l, bc, M, s->Lx[l] + b * C);
     }
     free(M);
   }
-  free(G);
   free(R);
-  free(T);
+}
+
+/* one cell's FMM-variant expansion (real layout), all from the particles:
+ * for sampled checks at sizes where the whole pass is too slow */
+int orc_fmm_local_cell(orc_sys *s, int l, const int c[3], double *out) {
+  if (l < 2 || l > s->L) return -1;
+  cplx *Lb = (cplx *)malloc(sizeof(cplx) * s->C);
+  fmm_target(s, l, c, NULL, Lb);
+  to_real_layout(s->p, Lb, out);
+  free(Lb);
+  return 0;
 }
 
 void orc_setup_fmm(orc_sys *s) {

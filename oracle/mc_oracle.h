@@ -55,6 +55,9 @@ void orc_destroy(orc_sys *s);
 void orc_setup(orc_sys *s);                       /* Alg. L.3 + K/E + U0 */
 /* FMM-variant initialisation: per-level multipoles + M2L over interaction lists */
 void orc_setup_fmm(orc_sys *s);
+/* one cell's FMM-variant expansion (real layout), source multipoles taken
+ * directly from the charges; -1 for a bad level */
+int orc_fmm_local_cell(orc_sys *s, int level, const int c[3], double *out);
 double orc_propose(orc_sys *s, int64_t j, const double rnew[3]);  /* Alg. L.1 */
 /* split of the last proposal: [0] expansions, [1] direct (Alg. 1 incl.
  * image correction), [2] far lattice, [3] dipole (tinfoil) term */

@@ -41,6 +41,10 @@ __global__ void k_energy_particles(const McSys*, double*);
 __global__ void k_energy_finish(const McSys*, int, const double*, double*);
 __global__ void k_lattice_sums(int, double*);
 __global__ void k_far_operator(int, double, const double*, double*);
+__global__ void k_p2m_level(const McSys*, int, int, double*);
+__global__ void k_offset_table(int, double*);
+cudaError_t m2l_launch(const McSys*, int, int, int, int, const double*, const double*, double*,
+                       cudaStream_t);
 
 struct mc_ctx {
   McSys h;        // host copy holding device pointers
@@ -57,6 +61,8 @@ struct mc_ctx {
   double* d_energy_tmp;  // fresh-energy target
   unsigned long long* d_prof;  // 32 timers when profiling is on, else null
   int schedule;                // MC_SCHEDULE_*
+  double* d_mpole;             // per-level multipoles (fast setup), allocated on first use
+  double* d_otab;              // offset harmonics table (fast setup)
   std::vector<void*> allocs;
 };
 
@@ -158,6 +164,50 @@ int run_setup(mc_ctx* c) {
     }
   }
   // K, dipole, H = G K
+  const int nch = std::min<int>(1024, std::max<int>(1, h.n / 64));
+  k_box_multipole<<<grid_for(c->sms, nch, MC_WARPS), MC_THREADS, 0, c->stream>>>(c->d_sys, nch,
+                                                                                c->d_scratch);
+  CK(cudaGetLastError());
+  k_far_finish<<<1, 256, 0, c->stream>>>(c->d_sys, nch, c->d_scratch);
+  CK(cudaGetLastError());
+  return MC_OK;
+}
+
+// FMM-variant initialisation (fast mode): multipoles of every level, then
+// multipole-to-local over the interaction lists
+int run_setup_fmm(mc_ctx* c) {
+  McSys& h = c->h;
+  const int C = h.C, p = h.p;
+  const int per = (2 * p + 1) * (2 * p + 2) / 2;
+  if (!c->d_mpole) {
+    if (dalloc(c, (void**)&c->d_mpole, sizeof(double) * (size_t)std::max(1, h.ncell_total) * C) != MC_OK ||
+        dalloc(c, (void**)&c->d_otab, sizeof(double) * 2 * 343 * (size_t)per) != MC_OK)
+      return MC_ERR_NOMEM;
+    k_offset_table<<<grid_for(c->sms, 343 * (size_t)per, 256), 256, 0, c->stream>>>(p, c->d_otab);
+    CK(cudaGetLastError());
+  }
+  for (int l = h.lmin; l <= h.L; l++) {
+    const int nl = h.lev_n[l], ncl = nl * nl * nl;
+    const int f = 1 << (h.L - l);
+    double* M = c->d_mpole + (size_t)h.lev_off[l] * C;
+    long long nchunk = std::min<long long>((long long)f * f * f,
+                                           std::max<long long>(1, (4LL * c->sms * MC_WARPS + ncl - 1) / ncl));
+    if (nchunk > 1 && (size_t)(ncl * nchunk * C) > c->scratch_doubles)
+      nchunk = std::max<long long>(1, (long long)(c->scratch_doubles / ((size_t)ncl * C)));
+    const long long ntask = (long long)ncl * nchunk;
+    k_p2m_level<<<grid_for(c->sms, (size_t)ntask, MC_WARPS), MC_THREADS, 0, c->stream>>>(
+        c->d_sys, l, (int)nchunk, nchunk > 1 ? c->d_scratch : M);
+    CK(cudaGetLastError());
+    if (nchunk > 1) {
+      k_reduce_chunks<<<grid_for(c->sms, (size_t)ncl * C, 256), 256, 0, c->stream>>>(
+          ncl, (int)nchunk, C, c->d_scratch, M);
+      CK(cudaGetLastError());
+    }
+  }
+  for (int l = h.lmin; l <= h.L; l++) {
+    CK(m2l_launch(c->d_sys, p, l, h.lev_n[l], c->sms, c->d_mpole + (size_t)h.lev_off[l] * C,
+                  c->d_otab, h.Lhat + (size_t)h.lev_off[l] * C, c->stream));
+  }
   const int nch = std::min<int>(1024, std::max<int>(1, h.n / 64));
   k_box_multipole<<<grid_for(c->sms, nch, MC_WARPS), MC_THREADS, 0, c->stream>>>(c->d_sys, nch,
                                                                                 c->d_scratch);
@@ -417,9 +467,9 @@ int mc_init(mc_ctx** out, int64_t n, const double* pos, const double* q, double 
 }
 
 int mc_setup(mc_ctx* c, int mode) {
-  if (!c || mode != MC_SETUP_P2L) return MC_ERR_ARG;
+  if (!c || (mode != MC_SETUP_P2L && mode != MC_SETUP_FMM)) return MC_ERR_ARG;
   CK(cudaSetDevice(c->dev));
-  int rc = run_setup(c);
+  int rc = mode == MC_SETUP_FMM ? run_setup_fmm(c) : run_setup(c);
   if (rc != MC_OK) return rc;
   rc = energy_into(c, c->h.energy);
   if (rc != MC_OK) return rc;

@@ -559,3 +559,285 @@ __global__ void k_far_operator(int p, double a, const double* __restrict__ St, d
     G[idx] = v;
   }
 }
+
+// ------------------------------------------ FMM-variant setup (fast mode)
+// Sec. 3.2, last paragraph: multipoles of every cell, then each cell's
+// Psi^Delta as the sum of multipole-to-local translations from the cells of
+// its interaction list (no local-to-local pass).  Scaled multipoles
+// Khat_n^m = sum q conj Rt_n^m(r - R_cell) are formed directly on every level.
+
+// one warp per (cell of level l, chunk of its finest cells); four charges per
+// step; chunk partials go to out[(cell * nchunk + chunk) * C] for
+// k_reduce_chunks (nchunk = 1 writes the level directly)
+__global__ void __launch_bounds__(MC_THREADS)
+    k_p2m_level(const McSys* __restrict__ sysp, int l, int nchunk, double* __restrict__ out) {
+  __shared__ McSys S;
+  __shared__ HarmTabs<double> tabs;
+  __shared__ double stage[MC_WARPS][256];
+  if (threadIdx.x == 0) S = *sysp;
+  harm_tabs_init<double>(&tabs);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane >> 3;
+  const int p = S.p, C = S.C, L = S.L, nL = S.nL;
+  const int nl = S.lev_n[l], f = 1 << (L - l);
+  const double w = S.lev_w[l];
+  const int nf = f * f * f, per = (nf + nchunk - 1) / nchunk;
+  const int ntask = nl * nl * nl * nchunk;
+  for (int task = blockIdx.x * MC_WARPS + warp; task < ntask; task += gridDim.x * MC_WARPS) {
+    const int t = task / nchunk, ch = task % nchunk;
+    const int tc[3] = {t / (nl * nl), (t / nl) % nl, t % nl};
+    const double Rx = (tc[0] + 0.5) * w, Ry = (tc[1] + 0.5) * w, Rz = (tc[2] + 0.5) * w;
+    double ar[MC_PMAX + 2], ai[MC_PMAX + 2];
+#pragma unroll
+    for (int q = 0; q <= MC_PMAX + 1; q++) ar[q] = ai[q] = 0.0;
+    const int fb = ch * per, fe = min(nf, fb + per);
+    for (int fc = fb; fc < fe; fc++) {
+      const int gx = tc[0] * f + fc / (f * f), gy = tc[1] * f + (fc / f) % f, gz = tc[2] * f + fc % f;
+      const int cell = (gx * nL + gy) * nL + gz;
+      const int cnt = S.ccount[cell];
+      for (int s0 = 0; s0 < cnt; s0 += 4) {
+        const int s = s0 + grp;
+        double4 v = make_double4(Rx, Ry, Rz, 0.0);  // inactive: zero charge at the centre
+        if (s < cnt) v = S.cpos[(size_t)cell * S.cap + s];
+        regular_group<double>(&tabs, p, v.x - Rx, v.y - Ry, v.z - Rz,
+                              [&](int t2, int n, int m, bool vld, double cr, double ci) {
+                                ar[t2] += v.w * cr;
+                                ai[t2] -= v.w * ci;
+                              });
+      }
+    }
+    double* st = stage[warp];
+#pragma unroll
+    for (int t2 = 0; t2 <= MC_PMAX + 1; t2++) {
+      double vr = ar[t2], vi = ai[t2];
+      vr += __shfl_xor_sync(0xffffffffu, vr, 8);
+      vi += __shfl_xor_sync(0xffffffffu, vi, 8);
+      vr += __shfl_xor_sync(0xffffffffu, vr, 16);
+      vi += __shfl_xor_sync(0xffffffffu, vi, 16);
+      int n, m;
+      bool vld;
+      group_nm(p, t2, &n, &m, &vld);
+      if (grp == 0 && vld) {
+        const int kk = rl_re(n, m);
+        st[kk] = vr;
+        if (m) st[kk + 1] = vi;
+      }
+    }
+    __syncwarp();
+    double* o = out + ((size_t)t * nchunk + ch) * C;
+    for (int kk = lane; kk < C; kk += 32) o[kk] = st[kk];
+    __syncwarp();
+  }
+}
+
+// It_l^mu(o), the scaled irregular harmonic at unit cell width, for every
+// integer offset o in [-3, 3]^3 (the interaction-list offsets are among
+// them), l <= 2p, 0 <= mu <= l: It = (l-mu)! (l+mu)! Rt / |o|^(2l+1).
+// Layout: [((ox+3)*7 + oy+3)*7 + oz+3][l(l+1)/2 + mu] complex (re, im).
+__global__ void k_offset_table(int p, double* __restrict__ out) {
+  const int lmax = 2 * p, per = (lmax + 1) * (lmax + 2) / 2;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < 343 * per;
+       idx += gridDim.x * blockDim.x) {
+    const int o = idx / per, r = idx % per;
+    int l = 0;
+    while ((l + 1) * (l + 2) / 2 <= r) l++;
+    const int mu = r - l * (l + 1) / 2;
+    const int ox = o / 49 - 3, oy = (o / 7) % 7 - 3, oz = o % 7 - 3;
+    double re = 0.0, im = 0.0;
+    if (ox || oy || oz) {
+      double hr, hi;
+      rt_single(l, mu, ox, oy, oz, &hr, &hi);
+      double f = 1.0;
+      for (int q = 2; q <= l - mu; q++) f *= q;
+      for (int q = 2; q <= l + mu; q++) f *= q;
+      const double r2 = (double)(ox * ox + oy * oy + oz * oz);
+      const double sc = f * pow(r2, -(l + 0.5));
+      re = hr * sc;
+      im = hi * sc;
+    }
+    out[2 * (size_t)idx] = re;
+    out[2 * (size_t)idx + 1] = im;
+  }
+}
+
+// Multipole-to-local over the interaction lists of level l.  With scaled
+// coefficients (Khat = M / s_n^m, Lhat = L s_j^k, s_n^m = sqrt((n-m)!(n+m)!))
+// the translation theorem of Greengard and Rokhlin for a source cell at
+// offset o (in cell widths w) from the target reads
+//   Lhat_j^k = w^-(j+1) sum_{n<=p} sum_{|m|<=n} (-1)^n sigma(k,m)
+//              It_{j+n}^{m-k}(o) w^-n Khat_n^m,   sigma(k,m) = (-1)^min(k,m)
+// for k, m >= 0 and 1 for m < 0 <= k; Khat^{n,-m} = conj Khat^{n,m} and
+// It^{l,-mu} = conj It^{l,mu}.  The m and -m terms are taken together, so
+// each (j, k; n, m > 0) needs four real coefficients, shared by the
+// MC_M2L_G targets a lane carries.
+// A CTA takes MC_M2L_T targets of one parity class, which share the 189
+// offsets: each offset's It table is staged once per CTA, each warp stages
+// its targets' source multipoles (scaled by (-1/w)^n), and lane q computes
+// the outputs q, q + 32, ... (j, k >= 0) of its warp's targets.
+#define MC_M2L_G 4
+#define MC_M2L_T (MC_WARPS * MC_M2L_G)
+__device__ __forceinline__ double flip_sign(double x, unsigned long long mask) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)mask);
+}
+
+template <int NS>
+__global__ void __launch_bounds__(MC_THREADS)
+    k_m2l_level(const McSys* __restrict__ sysp, int l, const double* __restrict__ Mlev,
+                const double* __restrict__ otab, double* __restrict__ Llev) {
+  __shared__ McSys S;
+  __shared__ unsigned short il[8][189];
+  extern __shared__ double dyn[];
+  if (threadIdx.x == 0) S = *sysp;
+  il_table_init(il);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p = S.p, C = S.C;
+  const bool pbc = S.bc == 0;
+  const int nl = S.lev_n[l], h = nl >> 1;
+  const double w = S.lev_w[l];
+  const int per = (2 * p + 1) * (2 * p + 2) / 2;
+  const int nout = (p + 1) * (p + 2) / 2;
+  double* tab = dyn;
+  double* src = dyn + 2 * per + (size_t)warp * MC_M2L_G * C;
+  int qj[NS], qk[NS];
+#pragma unroll
+  for (int u = 0; u < NS; u++) {
+    const int q = lane + 32 * u;
+    int j = 0;
+    while ((j + 1) * (j + 2) / 2 <= q) j++;
+    qj[u] = j;
+    qk[u] = q - j * (j + 1) / 2;
+  }
+  const int per_class = h * h * h;
+  const int chunks = (per_class + MC_M2L_T - 1) / MC_M2L_T;
+  for (int task = blockIdx.x; task < 8 * chunks; task += gridDim.x) {
+    const int cls = task / chunks;
+    const int i0 = (task % chunks) * MC_M2L_T + warp * MC_M2L_G;
+    const int bx = (cls >> 2) & 1, by = (cls >> 1) & 1, bz = cls & 1;
+    int tgt[MC_M2L_G][3];
+#pragma unroll
+    for (int g = 0; g < MC_M2L_G; g++) {
+      const int ii = min(i0 + g, per_class - 1);
+      tgt[g][0] = 2 * (ii / (h * h)) + bx;
+      tgt[g][1] = 2 * ((ii / h) % h) + by;
+      tgt[g][2] = 2 * (ii % h) + bz;
+    }
+    double accr[NS][MC_M2L_G], acci[NS][MC_M2L_G];
+#pragma unroll
+    for (int u = 0; u < NS; u++)
+#pragma unroll
+      for (int g = 0; g < MC_M2L_G; g++) accr[u][g] = acci[u][g] = 0.0;
+    for (int e = 0; e < 189; e++) {
+      int ox, oy, oz;
+      il_unpack(il[cls][e], &ox, &oy, &oz);
+      __syncthreads();  // previous offset's tables are consumed
+      const double* tb = otab + 2 * (size_t)(((ox + 3) * 7 + oy + 3) * 7 + oz + 3) * per;
+      for (int i = threadIdx.x; i < 2 * per; i += MC_THREADS) tab[i] = tb[i];
+#pragma unroll
+      for (int g = 0; g < MC_M2L_G; g++) {
+        const int e3[3] = {tgt[g][0] + ox, tgt[g][1] + oy, tgt[g][2] + oz};
+        bool ok = i0 + g < per_class;
+        int sc[3];
+        for (int d = 0; d < 3; d++) {
+          if (pbc) {
+            sc[d] = mc_wrap_coord(e3[d], nl);
+          } else {
+            sc[d] = e3[d];
+            if (e3[d] < 0 || e3[d] >= nl) ok = false;
+          }
+        }
+        const double* ms = Mlev + (size_t)((ok ? (sc[0] * nl + sc[1]) * nl + sc[2] : 0)) * C;
+        double* sg = src + g * C;
+        for (int i = lane; i < C; i += 32) {
+          int n = (int)sqrtf((float)i + 0.5f);
+          while (n * n > i) n--;
+          while ((n + 1) * (n + 1) <= i) n++;
+          sg[i] = ok ? ms[i] * ((n & 1) ? -1.0 : 1.0) * pow(w, -(double)n) : 0.0;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < NS; u++) {
+        if (lane + 32 * u >= nout) continue;
+        const int j = qj[u], k = qk[u];
+        for (int n = 0; n <= p; n++) {
+          const int L2 = j + n;
+          const double* t0 = tab + L2 * (L2 + 1);  // complex entry L2(L2+1)/2
+          const double* s0 = src + n * n;
+          {  // m = 0: It^{L2,-k} = conj It^{L2,k}
+            const double ar = t0[2 * k], ain = t0[2 * k + 1];
+#pragma unroll
+            for (int g = 0; g < MC_M2L_G; g++) {
+              const double kr = s0[g * C];
+              accr[u][g] = fma(ar, kr, accr[u][g]);
+              acci[u][g] = fma(-ain, kr, acci[u][g]);
+            }
+          }
+          for (int m = 1; m <= n; m++) {
+            const int d = m - k, ad = d < 0 ? -d : d;
+            const unsigned long long sgn = (unsigned long long)(min(k, m) & 1) << 63;
+            const double ar = flip_sign(t0[2 * ad], sgn);
+            const double ai = flip_sign(t0[2 * ad + 1], sgn ^ ((unsigned long long)(d < 0) << 63));
+            const double br = t0[2 * (m + k)], bir = t0[2 * (m + k) + 1];  // b = conj(br + i bir)
+            const double c1 = ar + br, c2n = ai + bir, c3 = ai - bir, c4 = ar - br;
+#pragma unroll
+            for (int g = 0; g < MC_M2L_G; g++) {
+              const double kr = s0[g * C + 2 * m - 1], ki = s0[g * C + 2 * m];
+              accr[u][g] = fma(kr, c1, fma(-ki, c2n, accr[u][g]));
+              acci[u][g] = fma(kr, c3, fma(ki, c4, acci[u][g]));
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < MC_M2L_G; g++) {
+      if (i0 + g >= per_class) continue;
+      double* o = Llev + (size_t)((tgt[g][0] * nl + tgt[g][1]) * nl + tgt[g][2]) * C;
+#pragma unroll
+      for (int u = 0; u < NS; u++) {
+        if (lane + 32 * u >= nout) continue;
+        const int j = qj[u], k = qk[u];
+        const double sc = pow(w, -(double)(j + 1));
+        const int kk = rl_re(j, k);
+        o[kk] = accr[u][g] * sc;
+        if (k) o[kk + 1] = acci[u][g] * sc;
+      }
+    }
+  }
+}
+
+size_t m2l_smem_bytes(int p) {
+  const int C = (p + 1) * (p + 1), per = (2 * p + 1) * (2 * p + 2) / 2;
+  return sizeof(double) * (2 * (size_t)per + (size_t)MC_WARPS * MC_M2L_G * C);
+}
+
+// launches the multipole-to-local pass of one level
+cudaError_t m2l_launch(const McSys* d_sys, int p, int l, int nl, int sms, const double* M,
+               const double* otab, double* Lout, cudaStream_t st) {
+  const int nout = (p + 1) * (p + 2) / 2, ns = (nout + 31) / 32;
+  const int h = nl / 2, chunks = (h * h * h + MC_M2L_T - 1) / MC_M2L_T;
+  const int grid = std::max(1, std::min(8 * chunks, sms * 4));
+  const size_t smem = m2l_smem_bytes(p);
+  cudaError_t e = cudaSuccess;
+#define MC_M2L_CASE(NS_)                                                                   \
+  case NS_:                                                                                \
+    e = cudaFuncSetAttribute(k_m2l_level<NS_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             (int)smem);                                                   \
+    if (e == cudaSuccess) {                                                                \
+      k_m2l_level<NS_><<<grid, MC_THREADS, smem, st>>>(d_sys, l, M, otab, Lout);           \
+      e = cudaGetLastError();                                                              \
+    }                                                                                      \
+    break;
+  switch (ns) {
+    MC_M2L_CASE(1)
+    MC_M2L_CASE(2)
+    MC_M2L_CASE(3)
+    MC_M2L_CASE(4)
+    MC_M2L_CASE(5)
+    default:
+      e = cudaErrorInvalidValue;
+  }
+#undef MC_M2L_CASE
+  return e;
+}

@@ -19,7 +19,7 @@ BC_PBC, BC_FREE = 0, 1
 TINFOIL, VACUUM = 0, 1
 FP64, FP32_EVAL = 0, 1
 SCHEDULE_PHASED, SCHEDULE_PIPELINED = 0, 1
-SETUP_P2L = 0
+SETUP_P2L, SETUP_FMM = 0, 1
 
 EXPORTED = ["mc_init", "mc_setup", "mc_propose", "mc_accept", "mc_run", "mc_energy",
             "mc_energy_fresh", "mc_get_positions", "mc_get_local", "mc_get_far",
