@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=5000, help="proposals per chain per batched step")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-huge", action="store_true", help="skip the N=1e6 setup/step leg")
+    ap.add_argument("--huge-steps", type=int, default=100_000,
+                    help="proposals timed per form on the N=1e6 workload")
     return ap.parse_args()
 
 
@@ -259,6 +262,51 @@ def batched_form(args, precision, stream, flush):
                 sizes=[n for n, _, _, _ in systems])
 
 
+def huge_workload_leg(args, stream, flush):
+    """N = 1e6 (density 0.1, 6 levels, p = 12): both setup modes timed with
+    CUDA events (each after one untimed call), the truncation-level gap of the
+    fast setup, then FP64 and FP32-eval chains of --huge-steps proposals."""
+    import torch
+
+    from paper_2006_16622_gb300 import mcfmm
+    from paper_2006_16622_gb300.workloads import HUGE as W
+
+    pos, q = W.system()
+    out = {"workload": W.name}
+
+    def timed(fn):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 1000.0
+
+    ctx = mcfmm.Context(pos, q, W.a, W.levels, W.p, stream=stream.cuda_stream)
+    energies = {}
+    for mode, name in ((mcfmm.SETUP_FMM, "fmm"), (mcfmm.SETUP_P2L, "p2l")):
+        ctx.setup(mode)
+        out[f"setup_{name}_s"] = timed(lambda: ctx.setup(mode))
+        energies[name] = ctx.energy()
+    out["fmm_energy_rel_gap"] = abs(energies["fmm"] - energies["p2l"]) / abs(energies["p2l"])
+    ctx.close()
+    for prec, name in ((mcfmm.FP64, "fp64"), (mcfmm.FP32_EVAL, "fp32_eval")):
+        ctx = mcfmm.Context(pos, q, W.a, W.levels, W.p, precision=prec, stream=stream.cuda_stream)
+        ctx.setup(mcfmm.SETUP_FMM)
+        ctx.run(5000, seed=W.seed, beta=W.beta, half_width=W.half_width, stats=False)
+        dt = timed(lambda: ctx.run(args.huge_steps, seed=W.seed + 1, beta=W.beta,
+                                   half_width=W.half_width, stats=False))
+        status = ctx.status()
+        ctx.close()
+        if status != 0:
+            raise RuntimeError(f"chain status {status}")
+        out[f"{name}_mh_steps_per_s"] = args.huge_steps / dt
+    out["mh_steps_timed"] = args.huge_steps
+    return out
+
+
 def precision_form_stats(W, stream):
     """FP32-eval vs the (oracle-parity-tested) FP64 chain on the same seed:
     per-proposal dE error over the common prefix of the two chains, and the
@@ -375,6 +423,7 @@ def gpu_arm(args):
         rb32 = batched_form(args, mcfmm.FP32_EVAL, stream, flush)
         rb64 = batched_form(args, mcfmm.FP64, stream, flush)
     prec_stats = None if args.no_precision else precision_form_stats(W, stream)
+    huge = None if (args.no_huge or rank != 0) else huge_workload_leg(args, stream, flush)
 
     # end to end through the C ABI: host arrays in, positions and energy out
     e2e = None
@@ -452,7 +501,7 @@ def gpu_arm(args):
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": args.steps, "clocks": r64["clocks"], "forms": forms,
             "precision_form": prec_stats,
-            "setup_s": r64["setup_s"]}
+            "setup_s": r64["setup_s"], "huge": huge}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

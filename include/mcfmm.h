@@ -144,6 +144,13 @@ int mc_status(mc_ctx *ctx);
 /* Wait-limit of the device-side grid barrier in nanoseconds (default 2e9);
  * a wait that runs out sets MC_ERR_TIMEOUT and the launch returns. */
 int mc_set_wait_limit(mc_ctx *ctx, int64_t ns);
+/* Failure-path testing (the paper has no counterpart): the grid barriers of
+ * the following mc_run calls on ctx also wait for missing_arrivals CTAs that
+ * never arrive, so the first wait runs out after the wait limit, the launch
+ * ends with MC_ERR_TIMEOUT before any accepted move is applied, and the
+ * context stays usable.  0 (the default) restores normal runs; 0..1024,
+ * else MC_ERR_ARG. */
+int mc_inject_wait_fault(mc_ctx *ctx, int missing_arrivals);
 /* Diagnostics: with profiling on, mc_run accumulates 32 device timers
  * (globaltimer nanoseconds) of its persistent launch: [0..4] CTA 0's own
  * propose items, first barrier wait, decision, own accept items, second

@@ -56,6 +56,7 @@ struct mc_ctx {
   int setup_done;
   long long steps_total;
   long long wait_ns;
+  unsigned bar_missing;  // mc_inject_wait_fault
   double* d_scratch;
   size_t scratch_doubles;
   double* d_energy_tmp;  // fresh-energy target
@@ -128,6 +129,7 @@ int sync_status(mc_ctx* c) {
 
 int launch_chain(mc_ctx* c, RunParams& rp) {
   rp.wait_ns = c->wait_ns;
+  rp.bar_missing = c->bar_missing;
   rp.prof = c->d_prof;
   const bool piped = rp.mode == 0 && c->schedule == MC_SCHEDULE_PIPELINED;
   rp.nf_cols = piped ? 4 : MC_NF_COLS;
@@ -483,7 +485,7 @@ int mc_propose(mc_ctx* c, int64_t j, const double r_new[3], double* dE_out) {
   if (!c->setup_done) return MC_ERR_STATE;
   if (!in_box(r_new, c->h.a)) return MC_ERR_OUTSIDE;
   CK(cudaSetDevice(c->dev));
-  RunParams rp;
+  RunParams rp{};
   memset(&rp, 0, sizeof(rp));
   rp.mode = 1;
   rp.nsteps = 1;
@@ -504,7 +506,7 @@ int mc_accept(mc_ctx* c, int64_t j, const double r_new[3], const double* dE_or_n
   if (!c->setup_done) return MC_ERR_STATE;
   if (!in_box(r_new, c->h.a)) return MC_ERR_OUTSIDE;
   CK(cudaSetDevice(c->dev));
-  RunParams rp;
+  RunParams rp{};
   memset(&rp, 0, sizeof(rp));
   rp.mode = 2;
   rp.nsteps = 1;
@@ -546,7 +548,7 @@ int mc_run(mc_ctx* c, int64_t n_steps, uint64_t seed, double beta, double half_w
   long long done = 0;
   int rc = MC_OK;
   while (done < n_steps || n_steps == 0) {
-    RunParams rp;
+    RunParams rp{};
     memset(&rp, 0, sizeof(rp));
     rp.mode = 0;
     rp.step0 = c->steps_total;
@@ -746,6 +748,12 @@ int mc_set_wait_limit(mc_ctx* c, int64_t ns) {
   return MC_OK;
 }
 
+int mc_inject_wait_fault(mc_ctx* c, int missing_arrivals) {
+  if (!c || missing_arrivals < 0 || missing_arrivals > 1024) return MC_ERR_ARG;
+  c->bar_missing = (unsigned)missing_arrivals;
+  return MC_OK;
+}
+
 }  // extern "C"
 
 // ------------------------------------------------------------------ batches
@@ -832,6 +840,7 @@ int batch_set_params(mc_batch* b, long long n_steps, const uint64_t* seeds, doub
     rp.beta = beta;
     rp.h = h;
     rp.wait_ns = b->ctxs[i]->wait_ns;
+    rp.bar_missing = 0u;
     rp.nf_cols = b->nf_cols;
     rp.chain = (unsigned)i;
     if (logj) {

@@ -399,7 +399,7 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
       rp.prof[0] += tp1 - tp0;
     }
     gen++;
-    if (!grid_barrier(S.bar, gen * (unsigned long long)nCTA, S.status, rp.wait_ns)) break;
+    if (!grid_barrier(S.bar, gen * (unsigned long long)(nCTA + rp.bar_missing), S.status, rp.wait_ns)) break;
     if (prof_lead) {
       tp0 = mc_globaltimer();
       rp.prof[1] += tp0 - tp1;
@@ -701,7 +701,7 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
       rp.prof[6] += 1;
     }
     gen++;
-    if (!grid_barrier(S.bar, gen * (unsigned long long)nCTA, S.status, rp.wait_ns)) break;
+    if (!grid_barrier(S.bar, gen * (unsigned long long)(nCTA + rp.bar_missing), S.status, rp.wait_ns)) break;
     if (prof_lead) rp.prof[4] += mc_globaltimer() - tp0;
     if (rp.stop_after_accepts > 0 && n_acc >= rp.stop_after_accepts) break;
   }

@@ -85,6 +85,8 @@ struct RunParams {
   unsigned long long* prof;  // optional phase/item timers (see mc_chain.cu), may be null
   int nf_cols;               // far-field column blocks per row block, 1..MC_NF_COLS
   unsigned chain;            // Philox counter word 2 (chain id)
+  unsigned bar_missing;      // arrivals each grid barrier waits for that never
+                             // come (failure-path tests; 0 in normal runs)
 };
 
 // ------------------------------------------------------------ error codes

@@ -835,7 +835,7 @@ __device__ __forceinline__ void chain_body_pipe(const McSys* __restrict__ sysp, 
       rp.prof[0] += tp1 - tp0;
     }
     gen++;
-    if (!grid_barrier(S.bar, gen * (unsigned long long)nCTA, S.status, rp.wait_ns)) break;
+    if (!grid_barrier(S.bar, gen * (unsigned long long)(nCTA + rp.bar_missing), S.status, rp.wait_ns)) break;
     if (prof_lead) {
       tp0 = mc_globaltimer();
       rp.prof[1] += tp0 - tp1;

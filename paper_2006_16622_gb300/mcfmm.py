@@ -26,7 +26,7 @@ EXPORTED = ["mc_init", "mc_setup", "mc_propose", "mc_accept", "mc_run", "mc_ener
             "mc_lattice_sums", "mc_status", "mc_set_wait_limit", "mc_profile", "mc_profile_read",
             "mc_destroy", "mc_strerror", "mc_p2l_level_noalloc", "mc_batch_create",
             "mc_batch_tune", "mc_batch_run", "mc_batch_info", "mc_batch_destroy",
-            "mc_set_schedule", "mc_batch_set_schedule"]
+            "mc_set_schedule", "mc_batch_set_schedule", "mc_inject_wait_fault"]
 
 
 class McStats(ctypes.Structure):
@@ -66,6 +66,7 @@ def load(path: str = LIB_PATH):
     L.mc_lattice_sums.argtypes = [I, P]
     L.mc_status.argtypes = [P]
     L.mc_set_wait_limit.argtypes = [P, I64]
+    L.mc_inject_wait_fault.argtypes = [P, ctypes.c_int]
     L.mc_profile.argtypes = [P, I]
     L.mc_profile_read.argtypes = [P, P]
     L.mc_p2l_level_noalloc.argtypes = [P, P, I64, D, I, I, I, I, P, P]
@@ -217,6 +218,10 @@ class Context:
 
     def set_wait_limit(self, ns):
         _check(load().mc_set_wait_limit(self._h, int(ns)), "mc_set_wait_limit")
+
+    def inject_wait_fault(self, missing_arrivals):
+        _check(load().mc_inject_wait_fault(self._h, int(missing_arrivals)),
+               "mc_inject_wait_fault")
 
 
 class Batch:
