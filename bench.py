@@ -371,9 +371,10 @@ def gpu_arm(args):
     S = args.mh_steps
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def time_form(precision):
+    def time_form(precision, schedule=mcfmm.SCHEDULE_PHASED):
         ctx = mcfmm.Context(pos, q, W.a, W.levels, W.p, precision=precision,
                             stream=stream.cuda_stream)
+        ctx.set_schedule(schedule)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx.setup()
@@ -416,7 +417,10 @@ def gpu_arm(args):
         return dict(total=tot, durs=durs, setup_s=setup_s, nu=nu, clocks=clocks)
 
     r64 = time_form(mcfmm.FP64)
-    r32 = None if args.no_fp32 else time_form(mcfmm.FP32_EVAL)
+    r32 = r32p = None
+    if not args.no_fp32:
+        r32 = time_form(mcfmm.FP32_EVAL)
+        r32p = time_form(mcfmm.FP32_EVAL, mcfmm.SCHEDULE_PLAIN)
 
     rb32 = rb64 = None
     if not args.no_batch:
@@ -477,6 +481,7 @@ def gpu_arm(args):
     forms = {"fp64": value}
     if r32:
         forms["fp32_eval"] = world * S * args.steps / r32["total"]
+        forms["fp32_eval_plain_schedule"] = world * S * args.steps / r32p["total"]
         forms["fp32_eval_acceptance"] = r32["nu"]
         forms["fp32_eval_setup_s"] = r32["setup_s"]
     if rb32:
@@ -496,6 +501,7 @@ def gpu_arm(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": W.name, "mh_steps_per_step": S, "form": "fp64",
+                       "schedule": "phased (speculative accept contributions)",
                        "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,

@@ -126,18 +126,25 @@ int mc_get_far(mc_ctx *ctx, double *K_out, double *H_out);
  * complex interleaved, index 2*(l*l + l + m). */
 int mc_lattice_sums(int lmax, double *out);
 /* Schedule of mc_run / mc_batch_run chains.
- *   MC_SCHEDULE_PHASED     (default) propose items, grid barrier, decision,
- *                          accept items, grid barrier: two barriers per
- *                          accepted step;
+ *   MC_SCHEDULE_PHASED     (default for mc_run) propose items, grid barrier,
+ *                          decision, accept items, grid barrier: two barriers
+ *                          per accepted step.  The Alg. L.2 contributions of
+ *                          the proposed move are computed during the
+ *                          proposal phase, on the warps the proposal leaves
+ *                          idle, and only added after the decision;
  *   MC_SCHEDULE_PIPELINED  the accept of step k runs in the same phase as the
  *                          proposal of step k+1 (one barrier per step); the
  *                          proposal sees the accepted state through
  *                          speculative coarse-level deltas and exact
  *                          Legendre-series corrections.  Same results to
  *                          roundoff; slower on GB300 in the measurements so
- *                          far (contention of the merged phase). */
+ *                          far (contention of the merged phase);
+ *   MC_SCHEDULE_PLAIN      (default for batches) as PHASED, with the Alg. L.2
+ *                          contributions computed after the decision (no
+ *                          work on rejected moves). */
 #define MC_SCHEDULE_PHASED 0
 #define MC_SCHEDULE_PIPELINED 1
+#define MC_SCHEDULE_PLAIN 2
 int mc_set_schedule(mc_ctx *ctx, int schedule);
 /* Status of the last asynchronous launch (MC_OK, MC_ERR_TIMEOUT, ...). */
 int mc_status(mc_ctx *ctx);
@@ -151,14 +158,17 @@ int mc_set_wait_limit(mc_ctx *ctx, int64_t ns);
  * context stays usable.  0 (the default) restores normal runs; 0..1024,
  * else MC_ERR_ARG. */
 int mc_inject_wait_fault(mc_ctx *ctx, int missing_arrivals);
-/* Diagnostics: with profiling on, mc_run accumulates 32 device timers
- * (globaltimer nanoseconds) of its persistent launch: [0..4] CTA 0's own
- * propose items, first barrier wait, decision, own accept items, second
- * barrier wait; [5] proposals, [6] accepts; [8+t], [16+t], [24+t] summed
+/* Diagnostics: with profiling on, mc_run accumulates MC_PROF_COUNTERS device
+ * timers (globaltimer nanoseconds) of its persistent launch: [0..4] CTA 0's
+ * own propose items, first barrier wait, decision, own accept items, second
+ * barrier wait; [5] proposals, [6] accepts; [8+t], [24+t], [40+t] summed
  * duration, count and maximum of work items of type t (0 expansion
  * evaluation, 1 near cell, 2 far lattice block, 3 image/dipole term,
- * 4 small-level accept entry, 5 accept target cell, 6 bookkeeping).
- * mc_profile_read copies them (out: 32 uint64) and clears them. */
+ * 4 small-level accept entry or apply, 5 accept target cell or apply,
+ * 6 bookkeeping and K/H, 7 speculative small-level contribution,
+ * 8 speculative large-level contribution).  mc_profile_read copies them
+ * (out: MC_PROF_COUNTERS uint64) and clears them. */
+#define MC_PROF_COUNTERS 56
 int mc_profile(mc_ctx *ctx, int on);
 int mc_profile_read(mc_ctx *ctx, uint64_t *out);
 void mc_destroy(mc_ctx *ctx);
@@ -191,7 +201,7 @@ int mc_batch_run(mc_batch *b, int64_t n_steps, const uint64_t *seeds, double bet
                  uint8_t *log_acc);
 /* CTAs given to each chain (n_chains ints) and the far-field tile count. */
 int mc_batch_info(mc_batch *b, int *ctas_out, int *nf_cols_out);
-/* Schedule of the batch's chains (MC_SCHEDULE_*, default phased). */
+/* Schedule of the batch's chains (MC_SCHEDULE_*, default plain). */
 int mc_batch_set_schedule(mc_batch *b, int schedule);
 void mc_batch_destroy(mc_batch *b);
 

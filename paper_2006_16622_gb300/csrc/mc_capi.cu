@@ -60,7 +60,7 @@ struct mc_ctx {
   double* d_scratch;
   size_t scratch_doubles;
   double* d_energy_tmp;  // fresh-energy target
-  unsigned long long* d_prof;  // 32 timers when profiling is on, else null
+  unsigned long long* d_prof;  // MC_PROF_COUNTERS timers when profiling is on, else null
   int schedule;                // MC_SCHEDULE_*
   double* d_mpole;             // per-level multipoles (fast setup), allocated on first use
   double* d_otab;              // offset harmonics table (fast setup)
@@ -133,6 +133,7 @@ int launch_chain(mc_ctx* c, RunParams& rp) {
   rp.prof = c->d_prof;
   const bool piped = rp.mode == 0 && c->schedule == MC_SCHEDULE_PIPELINED;
   rp.nf_cols = piped ? 4 : MC_NF_COLS;
+  rp.spec = c->schedule == MC_SCHEDULE_PHASED ? 1 : 0;
   rp.chain = 0u;
   CK(cudaMemsetAsync(c->h.bar, 0, sizeof(unsigned long long), c->stream));
   CK(cudaMemsetAsync(c->h.status, 0, sizeof(int), c->stream));
@@ -142,6 +143,9 @@ int launch_chain(mc_ctx* c, RunParams& rp) {
     CK(cudaMemsetAsync(c->h.dsmall, 0, sizeof(double) * 3 * (size_t)c->h.nsmall * c->h.C, c->stream));
     CK(mc_launch_pipe(c->d_sys, rp, c->h.prec, c->nCTA, c->stream));
   } else {
+    // the two small-level delta buffers of the speculative accept start clear
+    if (rp.spec && c->h.nsmall > 0)
+      CK(cudaMemsetAsync(c->h.dsmall, 0, sizeof(double) * 2 * (size_t)c->h.nsmall * c->h.C, c->stream));
     CK(mc_launch_chain(c->d_sys, rp, c->h.prec, c->nCTA, c->stream));
   }
   return MC_OK;
@@ -422,6 +426,8 @@ int mc_init(mc_ctx** out, int64_t n, const double* pos, const double* q, double 
   DA(h.dipv2, sizeof(double) * 3);
   DA(h.dsmall, sizeof(double) * 3 * (size_t)std::max(1, h.nsmall) * C);
   DA(h.sync, sizeof(unsigned long long) * 16);
+  DA(h.dacc, sizeof(double) * (size_t)(levels - h.lmin + 1) * MC_DSLOTS * C);
+  DA(h.dKpre, sizeof(double) * 2 * C);
   DCK(cudaMemsetAsync(h.dsmall, 0, sizeof(double) * 3 * (size_t)std::max(1, h.nsmall) * C, c->stream));
   DCK(cudaMemsetAsync(h.Khat, 0, sizeof(double) * C, c->stream));
   DCK(cudaMemsetAsync(h.Hhat, 0, sizeof(double) * C, c->stream));
@@ -713,8 +719,8 @@ int mc_profile(mc_ctx* c, int on) {
   if (!c) return MC_ERR_ARG;
   CK(cudaSetDevice(c->dev));
   if (on && !c->d_prof) {
-    if (dalloc(c, (void**)&c->d_prof, 32 * sizeof(unsigned long long)) != MC_OK) return MC_ERR_NOMEM;
-    CK(cudaMemset(c->d_prof, 0, 32 * sizeof(unsigned long long)));
+    if (dalloc(c, (void**)&c->d_prof, MC_PROF_COUNTERS * sizeof(unsigned long long)) != MC_OK) return MC_ERR_NOMEM;
+    CK(cudaMemset(c->d_prof, 0, MC_PROF_COUNTERS * sizeof(unsigned long long)));
   } else if (!on) {
     c->d_prof = nullptr;  // the buffer stays owned by the context
   }
@@ -726,13 +732,15 @@ int mc_profile_read(mc_ctx* c, uint64_t* out) {
   if (!c->d_prof) return MC_ERR_STATE;
   CK(cudaSetDevice(c->dev));
   CK(cudaStreamSynchronize(c->stream));
-  CK(cudaMemcpy(out, c->d_prof, 32 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
-  CK(cudaMemset(c->d_prof, 0, 32 * sizeof(unsigned long long)));
+  CK(cudaMemcpy(out, c->d_prof, MC_PROF_COUNTERS * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+  CK(cudaMemset(c->d_prof, 0, MC_PROF_COUNTERS * sizeof(unsigned long long)));
   return MC_OK;
 }
 
 int mc_set_schedule(mc_ctx* c, int schedule) {
-  if (!c || (schedule != MC_SCHEDULE_PHASED && schedule != MC_SCHEDULE_PIPELINED)) return MC_ERR_ARG;
+  if (!c || (schedule != MC_SCHEDULE_PHASED && schedule != MC_SCHEDULE_PIPELINED &&
+             schedule != MC_SCHEDULE_PLAIN))
+    return MC_ERR_ARG;
   c->schedule = schedule;
   return MC_OK;
 }
@@ -841,6 +849,7 @@ int batch_set_params(mc_batch* b, long long n_steps, const uint64_t* seeds, doub
     rp.h = h;
     rp.wait_ns = b->ctxs[i]->wait_ns;
     rp.bar_missing = 0u;
+    rp.spec = b->schedule == MC_SCHEDULE_PHASED ? 1 : 0;
     rp.nf_cols = b->nf_cols;
     rp.chain = (unsigned)i;
     if (logj) {
@@ -923,6 +932,7 @@ int mc_batch_create(mc_batch** out, int n_chains, mc_ctx* const* ctxs) {
     return MC_ERR_ARG;  // every chain needs at least one CTA
   }
   b->nf_cols = 4;
+  b->schedule = MC_SCHEDULE_PLAIN;
   std::vector<double> w(n_chains);
   for (int i = 0; i < n_chains; i++) w[i] = (double)(ctxs[i]->h.L - ctxs[i]->h.lmin + 1);
   b->ctas = split_by_weight(w, b->sms);
@@ -970,7 +980,9 @@ void mc_batch_destroy(mc_batch* b) {
 }
 
 int mc_batch_set_schedule(mc_batch* b, int schedule) {
-  if (!b || (schedule != MC_SCHEDULE_PHASED && schedule != MC_SCHEDULE_PIPELINED)) return MC_ERR_ARG;
+  if (!b || (schedule != MC_SCHEDULE_PHASED && schedule != MC_SCHEDULE_PIPELINED &&
+             schedule != MC_SCHEDULE_PLAIN))
+    return MC_ERR_ARG;
   b->schedule = schedule;
   if (b->g_valid) {
     cudaGraphExecDestroy(b->gexec);

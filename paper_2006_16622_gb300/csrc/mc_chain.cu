@@ -41,18 +41,19 @@ struct StepGeo {
   bool outside;  // free space: r' left the box
 };
 
-// Optional timers (RunParams.prof, 32 counters, globaltimer ns):
+// Optional timers (RunParams.prof, 56 counters, globaltimer ns):
 //   [0..4] CTA 0 thread 0: own propose items, barrier-1 wait, decision,
 //          own accept items, barrier-2 wait; [5] steps, [6] accepted steps;
-//   [8+t] summed duration, [16+t] count, [24+t] max duration of items of
-//   type t: 0 E, 1 N, 2 F, 3 X, 4 small-level accept, 5 target accept,
-//   6 bookkeeping.
+//   [8+t] summed duration, [24+t] count, [40+t] max duration of items of
+//   type t: 0 E, 1 N, 2 F, 3 X/U, 4 small-level accept (or apply),
+//   5 target accept (or apply), 6 bookkeeping and K/H, 7 speculative
+//   small-level contribution, 8 speculative large-level contribution.
 __device__ __forceinline__ void prof_item(unsigned long long* prof, int type,
                                           unsigned long long t0) {
   const unsigned long long d = mc_globaltimer() - t0;
   atomicAdd(&prof[8 + type], d);
-  atomicAdd(&prof[16 + type], 1ULL);
-  atomicMax(&prof[24 + type], d);
+  atomicAdd(&prof[24 + type], 1ULL);
+  atomicMax(&prof[40 + type], d);
 }
 
 __device__ __forceinline__ bool is_square(int k) {
@@ -63,6 +64,83 @@ __device__ __forceinline__ bool is_square(int k) {
 constexpr double kInf = __builtin_huge_val();
 
 }  // namespace
+
+// Offset of target cell tc from list centre c on a level with nl >= 8 cells
+// per axis: with periodic images the one image of the target within
+// [-nl/2, nl/2) per axis (an interaction-list offset lies in [-3, 3], so no
+// other image can be in the list).
+__device__ __forceinline__ void list_offset(const int* tc, const int* c, int nl, bool pbc, int* o) {
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    int v = tc[d] - c[d];
+    if (pbc) {
+      if (v >= nl / 2) v -= nl;
+      if (v < -nl / 2) v += nl;
+    }
+    o[d] = v;
+  }
+}
+
+// Target cell of large-level accept item k and whether the item owns it:
+// the interaction list of alpha' (items k < 189, or every item when alpha =
+// alpha' on this level) owns its targets; an item of the alpha list
+// (k >= 189) owns its target unless the target is also in IL(alpha').
+struct LargeItem {
+  int tc[3];
+  int ofs[3];  // offset of the target from the centre of the item's own list
+  bool owner, from_new;
+};
+
+__device__ __forceinline__ LargeItem large_item(const unsigned short (*il)[189], const int* co,
+                                                const int* cn, int nl, bool pbc, bool samel,
+                                                int k) {
+  LargeItem it;
+  it.owner = true;
+  it.from_new = samel || (k < 189);
+  const int kk = (k < 189) ? k : k - 189;
+  const int* base = it.from_new ? cn : co;
+  const int par = ((base[0] & 1) << 2) | ((base[1] & 1) << 1) | (base[2] & 1);
+  int ox, oy, oz;
+  il_unpack(il[par][kk], &ox, &oy, &oz);
+  it.ofs[0] = ox;
+  it.ofs[1] = oy;
+  it.ofs[2] = oz;
+  const int e[3] = {base[0] + ox, base[1] + oy, base[2] + oz};
+  if (!pbc && (e[0] < 0 || e[0] >= nl || e[1] < 0 || e[1] >= nl || e[2] < 0 || e[2] >= nl))
+    it.owner = false;
+  for (int d = 0; d < 3; d++) it.tc[d] = mc_wrap_coord(e[d], nl);
+  if (it.owner && !it.from_new) {
+    int o[3];
+    list_offset(it.tc, cn, nl, pbc, o);
+    if (in_il(o[0], o[1], o[2], cn[0], cn[1], cn[2])) it.owner = false;
+  }
+  return it;
+}
+
+// Small-level accept entry (levels with <= 4 cells per axis): entry `entry`
+// of IL(alpha) (side 0) or IL(alpha') (side 1); image copies make targets
+// repeat across entries, so updates of these levels are atomic adds.
+struct SmallEntry {
+  int t3[3];
+  int o[3];
+  bool valid;
+};
+
+__device__ __forceinline__ SmallEntry small_entry(const unsigned short (*il)[189], const int* cs,
+                                                  int nl, bool pbc, int entry) {
+  SmallEntry se;
+  const int par = ((cs[0] & 1) << 2) | ((cs[1] & 1) << 1) | (cs[2] & 1);
+  int ox = 0, oy = 0, oz = 0;
+  if (entry < 189) il_unpack(il[par][entry], &ox, &oy, &oz);
+  se.o[0] = ox;
+  se.o[1] = oy;
+  se.o[2] = oz;
+  const int e[3] = {cs[0] + ox, cs[1] + oy, cs[2] + oz};
+  se.valid = entry < 189 && (pbc || (e[0] >= 0 && e[0] < nl && e[1] >= 0 && e[1] < nl &&
+                                     e[2] >= 0 && e[2] < nl));
+  for (int d = 0; d < 3; d++) se.t3[d] = mc_wrap_coord(e[d], nl);
+  return se;
+}
 
 template <typename TE>
 __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunParams& rp,
@@ -95,12 +173,42 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
   const int p = S.p, C = S.C, L = S.L;
   const bool pbc = (S.bc == 0);
   const int nWarpsTot = nCTA * MC_WARPS;
+  const int gw = warp * nCTA + cta;  // this warp's first item of every phase
+  const bool spec = rp.spec != 0;
   unsigned long long gen = 0;
   long long n_acc = 0, n_border = 0, steps_done = 0;
   const bool prof_on = rp.prof != nullptr;
   const bool prof_lead = prof_on && cta == 0 && threadIdx.x == 0;
   unsigned long long tp0 = 0, tp1 = 0;
   const unsigned long long t_begin = mc_globaltimer();
+
+  // far lattice items come first, so far item f always runs on the warp of
+  // slot f: that warp keeps its block of the constant operator G (32 rows x
+  // csz columns) in registers for the whole launch
+  const int nRB = (C + 31) / 32;
+  const int nfc = rp.nf_cols;
+  const int nF = pbc ? nRB * nfc : 0;
+  const int csz = (C + nfc - 1) / nfc;
+  const bool gpre = nF <= nWarpsTot && csz <= MC_GPRE;
+  double gcol[MC_GPRE];
+#pragma unroll
+  for (int i = 0; i < MC_GPRE; i++) gcol[i] = 0.0;
+  if (gpre && gw < nF) {
+    const int k = (gw / nfc) * 32 + lane, cbeg = (gw % nfc) * csz;
+#pragma unroll
+    for (int i = 0; i < MC_GPRE; i++) {
+      const int c = cbeg + i;
+      if (k < C && i < csz && c < C) gcol[i] = __ldcg(&S.G[(size_t)c * C + k]);
+    }
+  }
+
+  // proposal of the next step, drawn and its particle loaded ahead (warp 0)
+  bool pf_ok = false;
+  int pf_j = 0;
+  double pf_d = 0.0, pf_u = 0.5;
+  double4 pf_pos = make_double4(0, 0, 0, 0);
+  bool prev_moved = false;  // the previous step moved particle sgeo.j
+  int prev_j = -1;          // (in every thread) the previous step's particle
 
   for (long long t = 0; t < rp.nsteps; t++) {
     const int buf = (int)(t & 1);
@@ -112,10 +220,22 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
       bool out = false;
       if (rp.mode == 0) {
         double d = 0.0;
-        mc_proposal_axis(rp.seed, (unsigned long long)(rp.step0 + t), rp.chain, S.n, rp.h,
-                         lane < 3 ? lane : 0, &j, &d, lane == 3 ? &uu : nullptr);
+        double4 pj;
+        if (pf_ok) {
+          j = pf_j;
+          d = pf_d;
+          uu = pf_u;
+          pj = pf_pos;
+          // the load was issued before the previous step's accept: if that
+          // step moved this particle, its position is the previous r'
+          if (prev_moved && j == sgeo.j && lane < 3)
+            pj = make_double4(sgeo.rn[0], sgeo.rn[1], sgeo.rn[2], sgeo.q);
+        } else {
+          mc_proposal_axis(rp.seed, (unsigned long long)(rp.step0 + t), rp.chain, S.n, rp.h,
+                           lane < 3 ? lane : 0, &j, &d, lane == 3 ? &uu : nullptr);
+          pj = lane < 3 ? ldcg4(&S.ppos[j]) : make_double4(0, 0, 0, 0);
+        }
         if (lane < 3) {
-          const double4 pj = ldcg4(&S.ppos[j]);
           q = pj.w;
           r = lane == 0 ? pj.x : (lane == 1 ? pj.y : pj.z);
           double x = __dadd_rn(r, d);
@@ -141,26 +261,36 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
       if (lane < 3) {
         cf = finest_coord(r, S.inv_wL, S.nL);
         cfn = any_out ? cf : finest_coord(rn, S.inv_wL, S.nL);
-        sgeo.r[lane] = r;
-        sgeo.rn[lane] = rn;
-        sgeo.cf[lane] = cf;
-        sgeo.cfn[lane] = cfn;
       }
+      // sgeo of the previous step is read above; all lanes have passed that
+      // point once the shuffles below have run
       // offsets from the cell centres: lane = side * 16 + level-slot, axis loop
+      double offv[3];
+      int lo = 0;
       {
         const int side = lane >> 4, li = lane & 15;
         const int l = L - li;
+        lo = (l >= 1 && l <= L && li <= L - 1) ? l : 0;
 #pragma unroll
         for (int ax = 0; ax < 3; ax++) {
           const double xo = __shfl_sync(0xffffffffu, r, ax), xn = __shfl_sync(0xffffffffu, rn, ax);
           const int co = __shfl_sync(0xffffffffu, cf, ax), cnn = __shfl_sync(0xffffffffu, cfn, ax);
           const double xs = side ? xn : xo;
           const int cs = side ? cnn : co;
-          if (l >= 1 && l <= L && li <= L - 1) {
-            const int c = cs >> (L - l);
-            s_off[side][l][ax] = xs - ((double)c + 0.5) * S.lev_w[l];
-          }
+          offv[ax] = lo ? xs - ((double)(cs >> (L - lo)) + 0.5) * S.lev_w[lo] : 0.0;
         }
+      }
+      __syncwarp();
+      if (lo) {
+        const int side = lane >> 4;
+#pragma unroll
+        for (int ax = 0; ax < 3; ax++) s_off[side][lo][ax] = offv[ax];
+      }
+      if (lane < 3) {
+        sgeo.r[lane] = r;
+        sgeo.rn[lane] = rn;
+        sgeo.cf[lane] = cf;
+        sgeo.cfn[lane] = cfn;
       }
       if (lane == 0) {
         sgeo.j = j;
@@ -168,32 +298,231 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
         sgeo.outside = any_out;
       }
       if (lane == 3) s_u = uu;
+      // draw the next proposal and start loading its particle
+      pf_ok = false;
+      if (rp.mode == 0 && t + 1 < rp.nsteps) {
+        mc_proposal_axis(rp.seed, (unsigned long long)(rp.step0 + t + 1), rp.chain, S.n, rp.h,
+                         lane < 3 ? lane : 0, &pf_j, &pf_d, lane == 3 ? &pf_u : nullptr);
+        if (lane < 3) pf_pos = ldcg4(&S.ppos[pf_j]);
+        pf_ok = true;
+      }
     }
     __syncthreads();
     const StepGeo g = sgeo;
     const double u = s_u;
     const bool nomove = (g.r[0] == g.rn[0] && g.r[1] == g.rn[1] && g.r[2] == g.rn[2]);
     const bool same = (g.cf[0] == g.cfn[0] && g.cf[1] == g.cfn[1] && g.cf[2] == g.cfn[2]);
+    const bool idle = nomove || g.outside;
 
-    // -------------------------------------------------------- propose items
+    // accept items per level: on small levels (<= 4 cells per axis) item k
+    // takes entries 2k, 2k+1 of IL(alpha) and IL(alpha') (4 contributions);
+    // on larger levels one item per updated target cell
+    int lev_items[MC_MAXLEV + 2], lev_start[MC_MAXLEV + 2];
+    int nD = 0;
+    for (int l = L; l >= S.lmin; l--) {
+      const int sh = L - l, nl = S.lev_n[l];
+      const bool samel = ((g.cf[0] >> sh) == (g.cfn[0] >> sh)) &&
+                         ((g.cf[1] >> sh) == (g.cfn[1] >> sh)) &&
+                         ((g.cf[2] >> sh) == (g.cfn[2] >> sh));
+      lev_items[l] = (nl <= 4) ? 95 : (samel ? 189 : 378);
+      lev_start[l] = nD;
+      nD += lev_items[l];
+    }
+    // speculative accept: phase-A items per level (small levels: as above,
+    // adding into the step's small-level delta buffer; large levels: two
+    // targets per item, staged in the level's block of MC_DSLOTS x C doubles
+    // at slot k) and phase-B apply items (one per small-level cell, two
+    // large-level targets per item)
+    int sp_items[MC_MAXLEV + 2], sp_start[MC_MAXLEV + 2];
+    int nDs = 0, nLB = 0;
+    for (int l = L; l >= S.lmin; l--) {
+      sp_items[l] = (S.lev_n[l] <= 4) ? 95 : (lev_items[l] + 1) / 2;
+      sp_start[l] = nDs;
+      nDs += sp_items[l];
+      if (S.lev_n[l] > 4) nLB += lev_items[l];
+    }
+    auto dslot = [&](int l, int slot) -> double* {
+      return S.dacc + ((size_t)(L - l) * MC_DSLOTS + slot) * C;
+    };
+    const size_t nsC = (size_t)S.nsmall * C;
+    double* dsm = S.dsmall + (size_t)(t & 1) * nsC;             // this step's
+    double* dsm_next = S.dsmall + (size_t)((t + 1) & 1) * nsC;  // zeroed now
+
+    // ------------------------------------- phase A: propose (+ accept deltas)
     const int nE = L - S.lmin + 1;
     const int nN = same ? 27 : 54;
-    const int nRB = (C + 31) / 32;
-    const int nfc = rp.nf_cols;
-    const int nF = pbc ? nRB * nfc : 0;
-    const int nItems = nE + nN + nF + 2;  // + X + U
+    const int iE = nF, iN = nF + nE, iX = nF + nE + nN, iU = iX + 1, iK = iU + 1;
+    // K: the far-field change dK of the next proposal, which depends on
+    // positions only, is formed one step ahead; this step's far items use
+    // the one formed in the previous step unless that step moved the
+    // particle this proposal picks
+    const bool k_next = pbc && rp.mode == 0 && t + 1 < rp.nsteps;
+    const bool dk_pre = pbc && rp.mode == 0 && t > 0 && !(prev_moved && g.j == prev_j);
+    const int nProp = k_next ? iK + 1 : iU + 1;
+    const int nPhaseA = nProp + ((spec && !idle) ? nDs : 0);
     double* part = S.partials + buf * MC_MAX_ITEMS;
 
-    for (int it = warp * nCTA + cta; it < nItems; it += nWarpsTot) {
+    for (int it = gw; it < nPhaseA; it += nWarpsTot) {
       const unsigned long long t_item = prof_on ? mc_globaltimer() : 0ULL;
+      int ptype = 7;
+      if (it >= nProp) {
+        // ---- speculative Alg. L.2 contributions of the proposed move
+        const int dk = it - nProp;
+        int l = L;
+        while (l > S.lmin && dk >= sp_start[l] + sp_items[l]) l--;
+        const int k = dk - sp_start[l];
+        const int sh = L - l, nl = S.lev_n[l];
+        const int co[3] = {g.cf[0] >> sh, g.cf[1] >> sh, g.cf[2] >> sh};
+        const int cn[3] = {g.cfn[0] >> sh, g.cfn[1] >> sh, g.cfn[2] >> sh};
+        const int grp = lane >> 3, side = grp & 1;
+        if (nl <= 4) {
+          // entries 2k, 2k+1 of both lists, added into the step's delta
+          // buffer of the small levels (image copies make targets repeat)
+          const SmallEntry se = small_entry(il, side ? cn : co, nl, pbc, 2 * k + (grp >> 1));
+          const TE f = se.valid ? from_double<TE>(side ? g.q : -g.q) : TE(0);
+          TE dx = TE(3), dy = TE(3), dz = TE(3);
+          if (se.valid) {
+            if (sizeof(TE) == 8) {
+              dx = (TE)(s_off[side][l][0] - s_kw[l][se.o[0] + 3]);
+              dy = (TE)(s_off[side][l][1] - s_kw[l][se.o[1] + 3]);
+              dz = (TE)(s_off[side][l][2] - s_kw[l][se.o[2] + 3]);
+            } else {
+              dx = from_double<TE>(s_off[side][l][0]) - s_kwe[l][se.o[0] + 3];
+              dy = from_double<TE>(s_off[side][l][1]) - s_kwe[l][se.o[1] + 3];
+              dz = from_double<TE>(s_off[side][l][2]) - s_kwe[l][se.o[2] + 3];
+            }
+          }
+          double* Dt = dsm + (size_t)(S.lev_off[l] + (se.t3[0] * nl + se.t3[1]) * nl + se.t3[2]) * C;
+          // FP32 evaluation: when alpha = alpha' on this level both sides of
+          // an entry hit the same target, so they are summed in the warp
+          // first (half the L2 atomics; in FP64 the adds would cost more)
+          const bool comb = sizeof(TE) == 4 && co[0] == cn[0] && co[1] == cn[1] && co[2] == cn[2];
+          irregular_group_s<TE>(&tabs, p, dx, dy, dz, f, [&](int t2, int n, int m, bool v, TE vr, TE vi) {
+            TE cr = vr, ci = vi;
+            if (comb) {
+              cr += __shfl_xor_sync(0xffffffffu, vr, 8);
+              ci += __shfl_xor_sync(0xffffffffu, vi, 8);
+            }
+            if (se.valid && v && !(comb && side)) {
+              const int kk = rl_re(n, m);
+              atomicAdd(&Dt[kk], to_double(cr));
+              if (m) atomicAdd(&Dt[kk + 1], to_double(neg_bits(ci)));
+            }
+          });
+        } else {
+          // targets 2k (groups 0, 1) and 2k+1 (groups 2, 3); group 0/2 the
+          // alpha side, 1/3 the alpha' side
+          const int kt = 2 * k + (grp >> 1);
+          const bool samel = lev_items[l] == 189;
+          const bool exists = kt < lev_items[l];
+          const LargeItem li = large_item(il, co, cn, nl, pbc, samel, exists ? kt : 0);
+          const bool own = exists && li.owner;
+          const int* cs = side ? cn : co;
+          int ofs[3] = {li.ofs[0], li.ofs[1], li.ofs[2]};
+          bool have = false;
+          if (own) {
+            if (samel || (li.from_new && side == 1) || (!li.from_new && side == 0)) {
+              have = true;
+            } else if (li.from_new) {
+              list_offset(li.tc, cs, nl, pbc, ofs);
+              have = in_il(ofs[0], ofs[1], ofs[2], cs[0], cs[1], cs[2]);
+            }  // else: the target is not in IL(alpha') (else not owner)
+          }
+          const TE f = have ? from_double<TE>(side ? g.q : -g.q) : TE(0);
+          TE dx = TE(3), dy = TE(3), dz = TE(3);
+          if (have) {
+            if (sizeof(TE) == 8) {
+              dx = (TE)(s_off[side][l][0] - s_kw[l][ofs[0] + 3]);
+              dy = (TE)(s_off[side][l][1] - s_kw[l][ofs[1] + 3]);
+              dz = (TE)(s_off[side][l][2] - s_kw[l][ofs[2] + 3]);
+            } else {
+              dx = from_double<TE>(s_off[side][l][0]) - s_kwe[l][ofs[0] + 3];
+              dy = from_double<TE>(s_off[side][l][1]) - s_kwe[l][ofs[1] + 3];
+              dz = from_double<TE>(s_off[side][l][2]) - s_kwe[l][ofs[2] + 3];
+            }
+          }
+          double* Ds = dslot(l, exists ? kt : 0);
+          irregular_group_s<TE>(&tabs, p, dx, dy, dz, f, [&](int t2, int n, int m, bool v, TE vr, TE vi) {
+            const TE cr = vr, ci = neg_bits(vi);
+            const TE orr = __shfl_xor_sync(0xffffffffu, cr, 8);
+            const TE oii = __shfl_xor_sync(0xffffffffu, ci, 8);
+            if (side == 0 && own && v) {
+              const int kk = rl_re(n, m);
+              __stcg(&Ds[kk], to_double(cr + orr));
+              if (m) __stcg(&Ds[kk + 1], to_double(ci + oii));
+            }
+          });
+        }
+        if (prof_on && lane == 0) prof_item(rp.prof, nl <= 4 ? 7 : 8, t_item);
+        continue;
+      }
+      if (spec) {
+        // clear the other small-level delta buffer (used again next step)
+        const size_t zc = (nsC + nProp - 1) / nProp, z0 = (size_t)it * zc;
+        const size_t z1 = z0 + zc < nsC ? z0 + zc : nsC;
+        for (size_t zi = z0 + lane; zi < z1; zi += 32) __stcg(&dsm_next[zi], 0.0);
+      }
       double partial = 0.0;
-      if (nomove || g.outside) {
+      if (idle) {
         // no work: dE is 0 (no move) or +inf (left a free-space box)
-        if (it == nItems - 2 && g.outside) partial = kInf;
-        if (it == nItems - 1 && lane == 0 && rp.mode == 0) part[MC_MAX_ITEMS - 1] = log(u);
-      } else if (it < nE) {
+        if (it == iX && g.outside) partial = kInf;
+        if (it == iU && lane == 0 && rp.mode == 0) part[MC_MAX_ITEMS - 1] = log(u);
+        ptype = 3;
+      } else if (it < nF) {
+        // ---- F: far lattice, Sec. 3.3 (iv) in the factored form
+        //   dU_inf = sum_k W_k dK_k (H_k + 1/2 (G dK)_k),  W = 1 (m = 0) or 2
+        ptype = 2;
+        const int f = it;
+        const int rb = f / nfc, cb = f % nfc;
+        const double c1 = 0.5 * S.a;
+        double* st = stage[warp];
+        const TE qe = from_double<TE>(g.q);
+        const int grp = lane >> 3;
+        const double* xg = (grp & 1) ? g.rn : g.r;
+        const int k = rb * 32 + lane;
+        const double hk = (cb == 0 && k < C) ? __ldcg(&S.Hhat[k]) : 0.0;
+        if (dk_pre) {
+          const double* src = S.dKpre + (size_t)(t & 1) * C;
+          for (int kk = lane; kk < C; kk += 32) st[kk] = __ldcg(&src[kk]);
+        } else {
+          const TE dx = from_double<TE>(xg[0] - c1), dy = from_double<TE>(xg[1] - c1),
+                   dz = from_double<TE>(xg[2] - c1);
+          regular_group_s<TE>(&tabs, p, dx, dy, dz, qe, [&](int t2, int n, int m, bool v, TE vr, TE vi) {
+            const TE nr = __shfl_xor_sync(0xffffffffu, vr, 8);
+            const TE ni = __shfl_xor_sync(0xffffffffu, vi, 8);
+            if (grp == 0 && v) {
+              // dK = q (conj Rt(r' - R1) - conj Rt(r - R1)), q folded into the sets
+              const int kk = rl_re(n, m);
+              st[kk] = to_double(nr - vr);
+              if (m) st[kk + 1] = to_double(vi - ni);
+            }
+          });
+        }
+        __syncwarp();
+        const int cbeg = cb * csz, cend = min(C, cbeg + csz);
+        double contrib = 0.0;
+        if (k < C) {
+          double gk = 0.0;
+          if (gpre && it == gw) {
+#pragma unroll
+            for (int i = 0; i < MC_GPRE; i++)
+              if (cbeg + i < cend) gk += gcol[i] * st[cbeg + i];
+          } else {
+            for (int c = cbeg; c < cend; c++) gk += __ldcg(&S.G[(size_t)c * C + k]) * st[c];
+          }
+          S.gK[(size_t)buf * MC_NF_COLS * C + (size_t)cb * C + k] = gk;
+          const double Wk = is_square(k) ? 1.0 : 2.0;
+          contrib = Wk * st[k] * (0.5 * gk + hk);
+        }
+        if (f == 0) {
+          for (int kk = lane; kk < C; kk += 32) S.dK[(size_t)buf * C + kk] = st[kk];
+        }
+        partial = warp_sum(contrib);
+        __syncwarp();
+      } else if (it < iN) {
         // ---- E: Eq. (2) at r (group 0) and r' (group 1) on level l
-        const int l = L - it, sh = L - l;
+        ptype = 0;
+        const int l = L - (it - iE), sh = L - l;
         const int grp = lane >> 3, side = grp & 1;
         const int* cc = side ? g.cfn : g.cf;
         const int cx = cc[0] >> sh, cy = cc[1] >> sh, cz = cc[2] >> sh;
@@ -217,16 +546,30 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
         }
         const TE dx = from_double<TE>(s_off[side][l][0]), dy = from_double<TE>(s_off[side][l][1]),
                  dz = from_double<TE>(s_off[side][l][2]);
-        TE acc = TE(0);
-        regular_group<TE>(&tabs, p, dx, dy, dz, [&](int t2, int n, int m, bool v, TE vr, TE vi) {
-          if (v) acc += (m ? TE(2) : TE(1)) * (Lr[t2] * vr - Li[t2] * vi);
-        });
+        // each lane contracts its two columns with the real column
+        // polynomials, then applies their diagonal values
+        const int m1 = lane & 7, len1 = p - m1 + 1;
+        TE SR = TE(0), SI = TE(0), SR1 = TE(0), SI1 = TE(0);
+        TE D1r, D1i, D2r, D2i;
+        regular_group_q<TE>(&tabs, p, dx, dy, dz, &D1r, &D1i, &D2r, &D2i,
+                            [&](int t2, int n, int m, bool v, bool c1, TE qv) {
+                              const bool sw = t2 == len1;  // first step of column 2
+                              SR1 = sw ? SR : SR1;
+                              SI1 = sw ? SI : SI1;
+                              SR = sw ? TE(0) : SR;
+                              SI = sw ? TE(0) : SI;
+                              const TE qs = v ? qv : TE(0);
+                              SR += Lr[t2] * qs;
+                              SI += Li[t2] * qs;
+                            });
+        TE acc = (m1 ? TE(2) : TE(1)) * (D1r * SR1 - D1i * SI1) + TE(2) * (D2r * SR - D2i * SI);
         acc = group_sum(acc);
         const TE accn = __shfl_sync(0xffffffffu, acc, 8);
         partial = g.q * to_double(accn - acc);
-      } else if (it < nE + nN) {
+      } else if (it < iX) {
         // ---- N: Alg. 1 over one near cell (27 cells of the extended domain)
-        const int k0 = it - nE;
+        ptype = 1;
+        const int k0 = it - iN;
         const int k = same ? k0 : (k0 % 27);
         const int side = same ? 2 : (k0 / 27);  // 0 old, 1 new, 2 both
         const int* cc = (side == 1) ? g.cfn : g.cf;
@@ -280,7 +623,6 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
             // FP32: slot positions are stored relative to their cell centre;
             // the query points relative to this (image) cell's centre follow
             // from their finest-cell offsets and the integer cell offset
-            // old point: cell offset of the near cell relative to cf
             const int oo0 = e0 - g.cf[0], oo1 = e1 - g.cf[1], oo2 = e2 - g.cf[2];
             const int on0 = e0 - g.cfn[0], on1 = e1 - g.cfn[1], on2 = e2 - g.cfn[2];
             const double wL = S.lev_w[L];
@@ -312,48 +654,10 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
           }
           if (__any_sync(0xffffffffu, ovl)) partial = kInf;
         }
-      } else if (it < nE + nN + nF) {
-        // ---- F: far lattice, Sec. 3.3 (iv) in the factored form
-        //   dU_inf = sum_k W_k dK_k (H_k + 1/2 (G dK)_k),  W = 1 (m = 0) or 2
-        const int f = it - nE - nN;
-        const int rb = f / nfc, cb = f % nfc;
-        const double c1 = 0.5 * S.a;
-        double* st = stage[warp];
-        const TE qe = from_double<TE>(g.q);
-        const int grp = lane >> 3;
-        const double* xg = (grp & 1) ? g.rn : g.r;
-        const TE dx = from_double<TE>(xg[0] - c1), dy = from_double<TE>(xg[1] - c1),
-                 dz = from_double<TE>(xg[2] - c1);
-        regular_group<TE>(&tabs, p, dx, dy, dz, [&](int t2, int n, int m, bool v, TE vr, TE vi) {
-          const TE nr = __shfl_xor_sync(0xffffffffu, vr, 8);
-          const TE ni = __shfl_xor_sync(0xffffffffu, vi, 8);
-          if (grp == 0 && v) {
-            // dK = q (conj Rt(r' - R1) - conj Rt(r - R1))
-            const int k = rl_re(n, m);
-            st[k] = to_double(qe * (nr - vr));
-            if (m) st[k + 1] = to_double(-qe * (ni - vi));
-          }
-        });
-        __syncwarp();
-        const int csz = (C + nfc - 1) / nfc;
-        const int cbeg = cb * csz, cend = min(C, cbeg + csz);
-        const int k = rb * 32 + lane;
-        double contrib = 0.0;
-        if (k < C) {
-          double gk = 0.0;
-          for (int c = cbeg; c < cend; c++) gk += S.G[(size_t)c * C + k] * st[c];
-          S.gK[(size_t)buf * MC_NF_COLS * C + (size_t)cb * C + k] = gk;
-          const double Wk = is_square(k) ? 1.0 : 2.0;
-          contrib = Wk * st[k] * (0.5 * gk + (cb == 0 ? __ldcg(&S.Hhat[k]) : 0.0));
-        }
-        if (f == 0) {
-          for (int kk = lane; kk < C; kk += 32) S.dK[(size_t)buf * C + kk] = st[kk];
-        }
-        partial = warp_sum(contrib);
-        __syncwarp();
-      } else if (it == nItems - 2) {
+      } else if (it == iX) {
         // ---- X: periodic self-interaction correction (Sec. 3.3, last item)
         //         and the dipole term (tinfoil reading)
+        ptype = 3;
         const TE q2 = from_double<TE>(g.q * g.q);
         const TE ddx = from_double<TE>(g.rn[0] - g.r[0]), ddy = from_double<TE>(g.rn[1] - g.r[1]),
                  ddz = from_double<TE>(g.rn[2] - g.r[2]);
@@ -385,13 +689,51 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
             partial += cdip * Dn2 - cdip * D2;
           }
         }
-      } else {
+      } else if (it == iU) {
         // ---- U: log(u) for the Metropolis test
+        ptype = 3;
         if (lane == 0 && rp.mode == 0) part[MC_MAX_ITEMS - 1] = log(u);
+      } else {
+        // ---- K: dK of the next proposal (drawn and moved exactly as the
+        //         proposal code of the next step does)
+        ptype = 2;
+        int jn;
+        double dn = 0.0;
+        mc_proposal_axis(rp.seed, (unsigned long long)(rp.step0 + t + 1), rp.chain, S.n, rp.h,
+                         lane < 3 ? lane : 0, &jn, &dn, nullptr);
+        const double4 pj = ldcg4(&S.ppos[jn]);
+        double x0 = 0.0, x1 = 0.0;
+        if (lane < 3) {
+          x0 = lane == 0 ? pj.x : (lane == 1 ? pj.y : pj.z);
+          double x = __dadd_rn(x0, dn);
+          if (x < 0.0) x = __dadd_rn(x, S.a);
+          if (x >= S.a) x = __dsub_rn(x, S.a);
+          x1 = x;
+        }
+        const int grp = lane >> 3, side = grp & 1;
+        const double c1 = 0.5 * S.a;
+        double xs[3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ax++) {
+          const double a0 = __shfl_sync(0xffffffffu, x0, ax), a1 = __shfl_sync(0xffffffffu, x1, ax);
+          xs[ax] = side ? a1 : a0;
+        }
+        const TE dx = from_double<TE>(xs[0] - c1), dy = from_double<TE>(xs[1] - c1),
+                 dz = from_double<TE>(xs[2] - c1);
+        double* dst = S.dKpre + (size_t)((t + 1) & 1) * C;
+        regular_group_s<TE>(&tabs, p, dx, dy, dz, from_double<TE>(pj.w),
+                            [&](int t2, int n, int m, bool v, TE vr, TE vi) {
+                              const TE nr = __shfl_xor_sync(0xffffffffu, vr, 8);
+                              const TE ni = __shfl_xor_sync(0xffffffffu, vi, 8);
+                              if (grp == 0 && v) {
+                                const int kk = rl_re(n, m);
+                                __stcg(&dst[kk], to_double(nr - vr));
+                                if (m) __stcg(&dst[kk + 1], to_double(vi - ni));
+                              }
+                            });
       }
       if (lane == 0) part[it] = partial;
-      if (prof_on && lane == 0)
-        prof_item(rp.prof, it < nE ? 0 : (it < nE + nN ? 1 : (it < nE + nN + nF ? 2 : 3)), t_item);
+      if (prof_on && lane == 0) prof_item(rp.prof, ptype, t_item);
     }
 
     if (prof_lead) {
@@ -407,12 +749,21 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
 
     // ------------------------------------------------ decision (every CTA)
     if (warp == 0) {
+      // the partials in one fixed order (loads issued together)
+      double v[MC_MAX_ITEMS / 32];
+#pragma unroll
+      for (int i = 0; i < MC_MAX_ITEMS / 32; i++) {
+        const int ii = lane + 32 * i;
+        v[i] = ii < nProp ? __ldcg(&part[ii]) : 0.0;
+      }
+      const double lu = (rp.mode == 0 && lane == 0) ? __ldcg(&part[MC_MAX_ITEMS - 1]) : 0.0;
       double acc = 0.0;
-      for (int i = lane; i < nItems; i += 32) acc += __ldcg(&part[i]);
+#pragma unroll
+      for (int i = 0; i < MC_MAX_ITEMS / 32; i++) acc += v[i];
       acc = warp_sum(acc);
       if (lane == 0) {
         s_dE = acc;
-        s_logu = (rp.mode == 0) ? __ldcg(&part[MC_MAX_ITEMS - 1]) : 0.0;
+        s_logu = lu;
       }
     }
     __syncthreads();
@@ -444,6 +795,8 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
       rp.prof[2] += tp1 - tp0;
       rp.prof[5] += 1;
     }
+    prev_moved = accept && !nomove;
+    prev_j = g.j;
     if (!accept || nomove) {
       if (accept) n_acc++;
       if (accept && cta == 0 && threadIdx.x == 0) S.energy[0] += dE_used;
@@ -452,26 +805,13 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
     }
     n_acc++;
 
-    // --------------------------------------------------------- accept items
-    // level item counts: on small levels (<= 4 cells per axis) item k takes
-    // entry k of IL(alpha) (half 0) and of IL(alpha') (half 1), each its own
-    // contribution; on larger levels one item per updated target cell: the
-    // interaction list of alpha' (owners) and of alpha (owners unless the
-    // target is also in IL(alpha')).
-    int lev_items[MC_MAXLEV + 2], lev_start[MC_MAXLEV + 2];
-    // item 0: bookkeeping; items 1..nKH: K and H += G dK, 32 entries each
+    // ----------------------------------------------- phase B: accept items
+    // item 0: bookkeeping; items 1..nKH: K and H += G dK, 32 entries each;
+    // then the Alg. L.2 items (applied from the staged contributions, or
+    // computed here when not speculating)
     const int nKH = pbc ? (C + 31) / 32 : 0;
-    int nA = 1 + nKH;
-    for (int l = L; l >= S.lmin; l--) {
-      const int sh = L - l, nl = S.lev_n[l];
-      const bool samel = ((g.cf[0] >> sh) == (g.cfn[0] >> sh)) &&
-                         ((g.cf[1] >> sh) == (g.cfn[1] >> sh)) &&
-                         ((g.cf[2] >> sh) == (g.cfn[2] >> sh));
-      lev_items[l] = (nl <= 4) ? 95 : (samel ? 189 : 378);
-      lev_start[l] = nA;
-      nA += lev_items[l];
-    }
-    for (int it = warp * nCTA + cta; it < nA; it += nWarpsTot) {
+    const int nB = 1 + nKH + (spec ? S.nsmall + nLB : nD);
+    for (int it = gw; it < nB; it += nWarpsTot) {
       const unsigned long long t_item = prof_on ? mc_globaltimer() : 0ULL;
       if (it == 0) {
         // ---- bookkeeping: K, H, dipole, energy, cell lists
@@ -550,108 +890,117 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
         continue;
       }
       // ---- Alg. L.2 items
+      if (spec) {
+        const int a = it - 1 - nKH;
+        if (a < S.nsmall) {
+          // small-level cell a (levels with <= 4 cells per axis are the
+          // first cells of Lhat): add the step's delta and clear it
+          double* Lt = S.Lhat + (size_t)a * C;
+          double* Dt = dsm + (size_t)a * C;
+          double v[8], w[8];
+#pragma unroll
+          for (int i = 0; i < 8; i++) {
+            const int kk = lane + 32 * i;
+            v[i] = kk < C ? __ldcg(&Lt[kk]) : 0.0;
+            w[i] = kk < C ? __ldcg(&Dt[kk]) : 0.0;
+          }
+#pragma unroll
+          for (int i = 0; i < 8; i++) {
+            const int kk = lane + 32 * i;
+            if (kk < C) {
+              __stcg(&Lt[kk], v[i] + w[i]);
+              __stcg(&Dt[kk], 0.0);
+            }
+          }
+          if (prof_on && lane == 0) prof_item(rp.prof, 4, t_item);
+          continue;
+        }
+        // large levels: staged target b of level l
+        int b = a - S.nsmall, l = L;
+        while (l > S.lmin && b >= lev_items[l]) {
+          b -= lev_items[l];
+          l--;
+        }
+        const int sh = L - l, nl = S.lev_n[l];
+        const int co[3] = {g.cf[0] >> sh, g.cf[1] >> sh, g.cf[2] >> sh};
+        const int cn[3] = {g.cfn[0] >> sh, g.cfn[1] >> sh, g.cfn[2] >> sh};
+        const LargeItem li = large_item(il, co, cn, nl, pbc, lev_items[l] == 189, b);
+        if (li.owner) {
+          const double* Ds = dslot(l, b);
+          double* Lt = S.Lhat + (size_t)(S.lev_off[l] + (li.tc[0] * nl + li.tc[1]) * nl + li.tc[2]) * C;
+          double v[8], w[8];
+#pragma unroll
+          for (int i = 0; i < 8; i++) {
+            const int kk = lane + 32 * i;
+            v[i] = kk < C ? __ldcg(&Lt[kk]) : 0.0;
+            w[i] = kk < C ? __ldcg(&Ds[kk]) : 0.0;
+          }
+#pragma unroll
+          for (int i = 0; i < 8; i++) {
+            const int kk = lane + 32 * i;
+            if (kk < C) __stcg(&Lt[kk], v[i] + w[i]);
+          }
+        }
+        if (prof_on && lane == 0) prof_item(rp.prof, 5, t_item);
+        continue;
+      }
+      const int dk = it - 1 - nKH;
       int l = L;
-      while (l > S.lmin && it >= lev_start[l] + lev_items[l]) l--;
-      const int k = it - lev_start[l];
+      while (l > S.lmin && dk >= lev_start[l] + lev_items[l]) l--;
+      const int k = dk - lev_start[l];
       const int sh = L - l, nl = S.lev_n[l];
       const int co[3] = {g.cf[0] >> sh, g.cf[1] >> sh, g.cf[2] >> sh};
       const int cn[3] = {g.cfn[0] >> sh, g.cfn[1] >> sh, g.cfn[2] >> sh};
+      const int grp = lane >> 3, side = grp & 1;
       if (nl <= 4) {
         // entries 2k (groups 0, 1) and 2k+1 (groups 2, 3) of IL(alpha)
-        // (groups 0, 2) and IL(alpha') (groups 1, 3); image copies make
-        // targets repeat across entries, so the update uses L2 atomic adds
-        const int grp = lane >> 3, side = grp & 1;
-        const int entry = 2 * k + (grp >> 1);
-        const int* cs = side ? cn : co;
-        const int par = ((cs[0] & 1) << 2) | ((cs[1] & 1) << 1) | (cs[2] & 1);
-        int ox = 0, oy = 0, oz = 0;
-        if (entry < 189) il_unpack(il[par][entry], &ox, &oy, &oz);
-        const int e[3] = {cs[0] + ox, cs[1] + oy, cs[2] + oz};
-        const bool valid = entry < 189 && (pbc || (e[0] >= 0 && e[0] < nl && e[1] >= 0 &&
-                                                   e[1] < nl && e[2] >= 0 && e[2] < nl));
-        const int t3[3] = {mc_wrap_coord(e[0], nl), mc_wrap_coord(e[1], nl),
-                           mc_wrap_coord(e[2], nl)};
-        const TE f = valid ? from_double<TE>(side ? g.q : -g.q) : TE(0);
+        // (groups 0, 2) and IL(alpha') (groups 1, 3), atomic adds
+        const SmallEntry se = small_entry(il, side ? cn : co, nl, pbc, 2 * k + (grp >> 1));
+        const TE f = se.valid ? from_double<TE>(side ? g.q : -g.q) : TE(0);
         TE dx = TE(3), dy = TE(3), dz = TE(3);
-        if (valid) {
+        if (se.valid) {
           if (sizeof(TE) == 8) {
-            dx = (TE)(s_off[side][l][0] - s_kw[l][ox + 3]);
-            dy = (TE)(s_off[side][l][1] - s_kw[l][oy + 3]);
-            dz = (TE)(s_off[side][l][2] - s_kw[l][oz + 3]);
+            dx = (TE)(s_off[side][l][0] - s_kw[l][se.o[0] + 3]);
+            dy = (TE)(s_off[side][l][1] - s_kw[l][se.o[1] + 3]);
+            dz = (TE)(s_off[side][l][2] - s_kw[l][se.o[2] + 3]);
           } else {
-            dx = from_double<TE>(s_off[side][l][0]) - s_kwe[l][ox + 3];
-            dy = from_double<TE>(s_off[side][l][1]) - s_kwe[l][oy + 3];
-            dz = from_double<TE>(s_off[side][l][2]) - s_kwe[l][oz + 3];
+            dx = from_double<TE>(s_off[side][l][0]) - s_kwe[l][se.o[0] + 3];
+            dy = from_double<TE>(s_off[side][l][1]) - s_kwe[l][se.o[1] + 3];
+            dz = from_double<TE>(s_off[side][l][2]) - s_kwe[l][se.o[2] + 3];
           }
         }
-        double* Lt = S.Lhat + (size_t)(S.lev_off[l] + (t3[0] * nl + t3[1]) * nl + t3[2]) * C;
-        irregular_group<TE>(&tabs, p, dx, dy, dz, [&](int t2, int n, int m, bool v, TE vr, TE vi) {
-          if (valid && v) {
+        double* Lt = S.Lhat + (size_t)(S.lev_off[l] + (se.t3[0] * nl + se.t3[1]) * nl + se.t3[2]) * C;
+        // FP32 evaluation: both sides of an entry summed in the warp when
+        // alpha = alpha' on this level (same target)
+        const bool comb = sizeof(TE) == 4 && co[0] == cn[0] && co[1] == cn[1] && co[2] == cn[2];
+        irregular_group_s<TE>(&tabs, p, dx, dy, dz, f, [&](int t2, int n, int m, bool v, TE vr, TE vi) {
+          TE cr = vr, ci = vi;
+          if (comb) {
+            cr += __shfl_xor_sync(0xffffffffu, vr, 8);
+            ci += __shfl_xor_sync(0xffffffffu, vi, 8);
+          }
+          if (se.valid && v && !(comb && side)) {
             const int kk = rl_re(n, m);
-            atomicAdd(&Lt[kk], to_double(f * vr));
-            if (m) atomicAdd(&Lt[kk + 1], to_double(-f * vi));
+            atomicAdd(&Lt[kk], to_double(cr));
+            if (m) atomicAdd(&Lt[kk + 1], to_double(neg_bits(ci)));
           }
         });
         if (prof_on && lane == 0) prof_item(rp.prof, 4, t_item);
         continue;
       }
-      int tc[3];
-      bool owner = true;
       const bool samel = lev_items[l] == 189;
-      const bool from_new = samel || (k < 189);
-      int o_known[3];
-      {
-        const int kk = (k < 189) ? k : k - 189;
-        const int* base = from_new ? cn : co;
-        const int par = ((base[0] & 1) << 2) | ((base[1] & 1) << 1) | (base[2] & 1);
-        int ox, oy, oz;
-        il_unpack(il[par][kk], &ox, &oy, &oz);
-        o_known[0] = ox;
-        o_known[1] = oy;
-        o_known[2] = oz;
-        const int e[3] = {base[0] + ox, base[1] + oy, base[2] + oz};
-        if (!pbc && (e[0] < 0 || e[0] >= nl || e[1] < 0 || e[1] >= nl || e[2] < 0 || e[2] >= nl))
-          owner = false;
-        for (int d = 0; d < 3; d++) tc[d] = mc_wrap_coord(e[d], nl);
-        if (owner && !from_new) {
-          // skip targets that the alpha' list owns
-          for (int s = 0; s < 27 && owner; s++) {
-            const int sx = s / 9 - 1, sy = (s / 3) % 3 - 1, sz = s % 3 - 1;
-            if (!pbc && (sx || sy || sz)) continue;
-            if (in_il(tc[0] + sx * nl - cn[0], tc[1] + sy * nl - cn[1], tc[2] + sz * nl - cn[2],
-                      cn[0], cn[1], cn[2]))
-              owner = false;
-          }
-        }
-      }
-      if (!owner) continue;
-      // this side's contribution (group 0 old, group 1 new; groups 2, 3
-      // repeat them): the (at most one, nl >= 8) image of the target inside
-      // the side's interaction list.  The offset is known for the list the
-      // item came from (and for both sides when alpha = alpha' on this
-      // level); only the other side of a mixed item searches.
-      const int grp = lane >> 3, side = grp & 1;
+      const LargeItem li = large_item(il, co, cn, nl, pbc, samel, k);
+      if (!li.owner) continue;
       const int* cs = side ? cn : co;
-      int ofs[3] = {o_known[0], o_known[1], o_known[2]};
+      int ofs[3] = {li.ofs[0], li.ofs[1], li.ofs[2]};
       bool have;
-      if (samel || (from_new && side == 1) || (!from_new && side == 0)) {
+      if (samel || (li.from_new && side == 1) || (!li.from_new && side == 0)) {
         have = true;
-      } else if (!from_new) {
+      } else if (!li.from_new) {
         have = false;  // the target is not in IL(alpha') (else not owner)
       } else {
-        have = false;
-        for (int s = 0; s < 27 && !have; s++) {
-          const int sx = s / 9 - 1, sy = (s / 3) % 3 - 1, sz = s % 3 - 1;
-          if (!pbc && (sx || sy || sz)) continue;
-          const int o0 = tc[0] + sx * nl - cs[0], o1 = tc[1] + sy * nl - cs[1],
-                    o2 = tc[2] + sz * nl - cs[2];
-          if (in_il(o0, o1, o2, cs[0], cs[1], cs[2])) {
-            have = true;
-            ofs[0] = o0;
-            ofs[1] = o1;
-            ofs[2] = o2;
-          }
-        }
+        list_offset(li.tc, cs, nl, pbc, ofs);
+        have = in_il(ofs[0], ofs[1], ofs[2], cs[0], cs[1], cs[2]);
       }
       const TE f = have ? from_double<TE>(side ? g.q : -g.q) : TE(0);
       TE dx = TE(3), dy = TE(3), dz = TE(3);
@@ -667,8 +1016,8 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
         }
       }
       double* st = stage[warp];
-      irregular_group<TE>(&tabs, p, dx, dy, dz, [&](int t2, int n, int m, bool v, TE vr, TE vi) {
-        const TE cr = f * vr, ci = -f * vi;
+      irregular_group_s<TE>(&tabs, p, dx, dy, dz, f, [&](int t2, int n, int m, bool v, TE vr, TE vi) {
+        const TE cr = vr, ci = neg_bits(vi);
         const TE orr = __shfl_xor_sync(0xffffffffu, cr, 8);
         const TE oii = __shfl_xor_sync(0xffffffffu, ci, 8);
         if (grp == 0 && v) {
@@ -678,7 +1027,7 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
         }
       });
       __syncwarp();
-      double* Lt = S.Lhat + (size_t)(S.lev_off[l] + (tc[0] * nl + tc[1]) * nl + tc[2]) * C;
+      double* Lt = S.Lhat + (size_t)(S.lev_off[l] + (li.tc[0] * nl + li.tc[1]) * nl + li.tc[2]) * C;
       {
         double v[8];
 #pragma unroll

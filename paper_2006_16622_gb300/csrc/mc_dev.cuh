@@ -30,6 +30,8 @@
 #define MC_MAX_ITEMS 256
 #define MC_NF_ROWS 6    // far-field row blocks of 32 rows (covers C <= 192)
 #define MC_NF_COLS 16   // far-field column chunks (maximum; RunParams.nf_cols <= this)
+#define MC_GPRE 16      // far-operator columns a warp keeps in registers
+#define MC_DSLOTS 380   // staged accept contributions per level (>= 378 targets)
 
 // ---------------------------------------------------------------- state
 struct McSys {
@@ -66,6 +68,9 @@ struct McSys {
   int ls_end;        // first level with more than 4 cells per axis (or L + 1)
   int nsmall;        // cells of levels lmin .. ls_end-1 (the first cells of Lhat)
   unsigned long long* sync;  // [16]: [l] read epoch of level l, [12] near items done
+  // speculative accept: Alg. L.2 contributions staged during the proposal
+  double* dacc;      // [(L - lmin + 1) * MC_DSLOTS * C]
+  double* dKpre;     // [2 * C] dK of the next proposal, by step parity
 };
 
 struct RunParams {
@@ -87,6 +92,8 @@ struct RunParams {
   unsigned chain;            // Philox counter word 2 (chain id)
   unsigned bar_missing;      // arrivals each grid barrier waits for that never
                              // come (failure-path tests; 0 in normal runs)
+  int spec;                  // 1: Alg. L.2 contributions computed during the
+                             // proposal phase, applied after the decision
 };
 
 // ------------------------------------------------------------ error codes
@@ -416,6 +423,107 @@ __device__ __forceinline__ void irregular_group(const HarmTabs<T>* t, int p, T x
   const T ir2 = ir * ir;
   harm_group<T>(t->iA, t->iB, p, x * ir2, y * ir2, z * ir2, ir2, ir, use);
 }
+
+// The same sets times a factor s (the recurrence is linear in its start
+// value, so the factor costs one multiply instead of one per coefficient).
+template <typename T, typename F>
+__device__ __forceinline__ void regular_group_s(const HarmTabs<T>* t, int p, T x, T y, T z, T s,
+                                                F&& use) {
+  const T r2 = x * x + y * y + z * z;
+  harm_group<T>(t->rA, t->rB, p, x, y, z, r2, s, use);
+}
+
+template <typename T, typename F>
+__device__ __forceinline__ void irregular_group_s(const HarmTabs<T>* t, int p, T x, T y, T z, T s,
+                                                  F&& use) {
+  const T r2 = x * x + y * y + z * z;
+  const T ir = mc_rsqrt(r2);
+  const T ir2 = ir * ir;
+  harm_group<T>(t->iA, t->iB, p, x * ir2, y * ir2, z * ir2, ir2, ir * s, use);
+}
+
+// Column factorisation: every scaled harmonic of column m is the diagonal
+// value X_m^m times a real polynomial q_n^m(z, r^2) with q_m^m = 1 and the
+// same two-term recurrence, so a consumer that contracts a whole column
+// with coefficients (the evaluation of Eq. 2) runs the recurrence on reals
+// (4 flops per step instead of 6) and applies X_m^m once per column.
+// use(t, n, m, valid, first_column, q); the diagonal values of this lane's
+// two columns are returned in (d1r, d1i), (d2r, d2i).
+template <typename T, typename F>
+__device__ __forceinline__ void harm_group_q(const T (*A)[16], const T (*B)[16], int p, T X, T Y,
+                                             T Z, T Q, T start, T* d1r_out, T* d1i_out, T* d2r_out,
+                                             T* d2i_out, F&& use) {
+  const int g = threadIdx.x & 7;
+  const int k0 = 2 * g, k1 = 2 * g + 1;
+  const T a0 = A[k0][k0], a1 = A[k1][k1];
+  T f0r = (k0 == 0) ? start : X * a0, f0i = (k0 == 0) ? T(0) : Y * a0;
+  const T f1r = X * a1, f1i = Y * a1;
+  T Pr, Pi;
+  cmul(f0r, f0i, f1r, f1i, &Pr, &Pi);
+  T Ir = Pr, Ii = Pi;
+#pragma unroll
+  for (int d = 1; d < 8; d <<= 1) {
+    const T ur = __shfl_up_sync(0xffffffffu, Ir, d, 8), ui = __shfl_up_sync(0xffffffffu, Ii, d, 8);
+    if (g >= d) {
+      T nr, ni;
+      cmul(ur, ui, Ir, Ii, &nr, &ni);
+      Ir = nr;
+      Ii = ni;
+    }
+  }
+  T Er = __shfl_up_sync(0xffffffffu, Ir, 1, 8), Ei = __shfl_up_sync(0xffffffffu, Ii, 1, 8);
+  if (g == 0) {
+    Er = T(1);
+    Ei = T(0);
+  }
+  T D0r, D0i;
+  cmul(Er, Ei, f0r, f0i, &D0r, &D0i);
+  const T D1r = Ir, D1i = Ii;
+  const int m1 = g, m2 = p - g;
+  const bool active = m1 <= m2;
+  const bool two = m2 > m1;
+  const T e1r = __shfl_sync(0xffffffffu, D0r, m1 >> 1, 8), e1i = __shfl_sync(0xffffffffu, D0i, m1 >> 1, 8);
+  const T o1r = __shfl_sync(0xffffffffu, D1r, m1 >> 1, 8), o1i = __shfl_sync(0xffffffffu, D1i, m1 >> 1, 8);
+  const int m2c = (m2 >= 0 && m2 <= 15) ? m2 : 0;
+  const T e2r = __shfl_sync(0xffffffffu, D0r, m2c >> 1, 8), e2i = __shfl_sync(0xffffffffu, D0i, m2c >> 1, 8);
+  const T o2r = __shfl_sync(0xffffffffu, D1r, m2c >> 1, 8), o2i = __shfl_sync(0xffffffffu, D1i, m2c >> 1, 8);
+  *d1r_out = (m1 & 1) ? o1r : e1r;
+  *d1i_out = (m1 & 1) ? o1i : e1i;
+  *d2r_out = (m2c & 1) ? o2r : e2r;
+  *d2i_out = (m2c & 1) ? o2i : e2i;
+  const int len1 = p - m1 + 1;
+  T q1 = T(0), q2 = T(0);
+#pragma unroll
+  for (int t = 0; t <= MC_PMAX + 1; t++) {
+    if (t <= p + 1) {
+      const bool c1 = t < len1;
+      const int m = c1 ? m1 : m2c;
+      const int n = c1 ? (m1 + t) : (m2c + t - len1);
+      const bool valid = active && (c1 || two) && n <= p;
+      const bool st = (n == m);
+      const int nn = n > 15 ? 15 : n;
+      const T a = Z * A[nn][m], b = Q * B[nn][m];
+      T v = a * q1 - b * q2;
+      v = st ? T(1) : v;
+      q2 = st ? T(0) : q1;
+      q1 = v;
+      use(t, n, m, valid, c1, v);
+    }
+  }
+}
+
+template <typename T, typename F>
+__device__ __forceinline__ void regular_group_q(const HarmTabs<T>* t, int p, T x, T y, T z, T* d1r,
+                                                T* d1i, T* d2r, T* d2i, F&& use) {
+  const T r2 = x * x + y * y + z * z;
+  harm_group_q<T>(t->rA, t->rB, p, x, y, z, r2, T(1), d1r, d1i, d2r, d2i, use);
+}
+
+// sign flip on the integer pipe (a negation alone would be an FP64 op)
+__device__ __forceinline__ double neg_bits(double x) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
+}
+__device__ __forceinline__ float neg_bits(float x) { return -x; }
 
 // index of (n, m) in the real layout (re part; im part is +1 for m > 0)
 __device__ __forceinline__ int rl_re(int n, int m) { return n * n + (m ? 2 * m - 1 : 0); }

@@ -44,8 +44,8 @@ __device__ __forceinline__ bool sq(int k) {
 __device__ __forceinline__ void p_prof(unsigned long long* prof, int type, unsigned long long t0) {
   const unsigned long long d = mc_globaltimer() - t0;
   atomicAdd(&prof[8 + type], d);
-  atomicAdd(&prof[16 + type], 1ULL);
-  atomicMax(&prof[24 + type], d);
+  atomicAdd(&prof[24 + type], 1ULL);
+  atomicMax(&prof[40 + type], d);
 }
 
 // bounded wait until *w >= target; false (and status set) on timeout

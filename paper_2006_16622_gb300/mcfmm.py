@@ -18,8 +18,9 @@ MC_OK = 0
 BC_PBC, BC_FREE = 0, 1
 TINFOIL, VACUUM = 0, 1
 FP64, FP32_EVAL = 0, 1
-SCHEDULE_PHASED, SCHEDULE_PIPELINED = 0, 1
+SCHEDULE_PHASED, SCHEDULE_PIPELINED, SCHEDULE_PLAIN = 0, 1, 2
 SETUP_P2L, SETUP_FMM = 0, 1
+PROF_COUNTERS = 56
 
 EXPORTED = ["mc_init", "mc_setup", "mc_propose", "mc_accept", "mc_run", "mc_energy",
             "mc_energy_fresh", "mc_get_positions", "mc_get_local", "mc_get_far",
@@ -209,7 +210,7 @@ class Context:
         _check(load().mc_profile(self._h, 1 if on else 0), "mc_profile")
 
     def profile_read(self):
-        out = np.zeros(32, dtype=np.uint64)
+        out = np.zeros(PROF_COUNTERS, dtype=np.uint64)
         _check(load().mc_profile_read(self._h, _ptr(out)), "mc_profile_read")
         return out
 
