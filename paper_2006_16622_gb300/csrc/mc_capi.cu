@@ -145,7 +145,7 @@ int launch_chain(mc_ctx* c, RunParams& rp) {
   } else {
     // the two small-level delta buffers of the speculative accept start clear
     if (rp.spec && c->h.nsmall > 0)
-      CK(cudaMemsetAsync(c->h.dsmall, 0, sizeof(double) * 2 * (size_t)c->h.nsmall * c->h.C, c->stream));
+      CK(cudaMemsetAsync(c->h.dsmall, 0, sizeof(double) * 3 * (size_t)c->h.nsmall * c->h.C, c->stream));
     CK(mc_launch_chain(c->d_sys, rp, c->h.prec, c->nCTA, c->stream));
   }
   return MC_OK;
@@ -426,7 +426,7 @@ int mc_init(mc_ctx** out, int64_t n, const double* pos, const double* q, double 
   DA(h.dipv2, sizeof(double) * 3);
   DA(h.dsmall, sizeof(double) * 3 * (size_t)std::max(1, h.nsmall) * C);
   DA(h.sync, sizeof(unsigned long long) * 16);
-  DA(h.dacc, sizeof(double) * (size_t)(levels - h.lmin + 1) * MC_DSLOTS * C);
+  DA(h.dacc, sizeof(double) * 2 * (size_t)(levels - h.lmin + 1) * MC_DSLOTS * C);
   DA(h.dKpre, sizeof(double) * 2 * C);
   DCK(cudaMemsetAsync(h.dsmall, 0, sizeof(double) * 3 * (size_t)std::max(1, h.nsmall) * C, c->stream));
   DCK(cudaMemsetAsync(h.Khat, 0, sizeof(double) * C, c->stream));

@@ -182,19 +182,24 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
   unsigned long long tp0 = 0, tp1 = 0;
   const unsigned long long t_begin = mc_globaltimer();
 
-  // far lattice items come first, so far item f always runs on the warp of
-  // slot f: that warp keeps its block of the constant operator G (32 rows x
-  // csz columns) in registers for the whole launch
+  // Proposal items in the order F, E, N, X, U, K.  The far items come
+  // first, so far item f always runs on the warp of slot f, which keeps its
+  // block of the constant operator G (32 rows x csz columns) in registers for
+  // the launch.  (The items share SMs with the speculative accept items that
+  // follow them; measured on GB300, this order leaves the expansion items on
+  // the SMs with the fewest of those.)
   const int nRB = (C + 31) / 32;
   const int nfc = rp.nf_cols;
   const int nF = pbc ? nRB * nfc : 0;
   const int csz = (C + nfc - 1) / nfc;
+  const int nE = L - S.lmin + 1;
   const bool gpre = nF <= nWarpsTot && csz <= MC_GPRE;
+  const int gf = gw;  // far item of this warp's slot
   double gcol[MC_GPRE];
 #pragma unroll
   for (int i = 0; i < MC_GPRE; i++) gcol[i] = 0.0;
-  if (gpre && gw < nF) {
-    const int k = (gw / nfc) * 32 + lane, cbeg = (gw % nfc) * csz;
+  if (gpre && gf >= 0 && gf < nF) {
+    const int k = (gf / nfc) * 32 + lane, cbeg = (gf % nfc) * csz;
 #pragma unroll
     for (int i = 0; i < MC_GPRE; i++) {
       const int c = cbeg + i;
@@ -207,8 +212,16 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
   int pf_j = 0;
   double pf_d = 0.0, pf_u = 0.5;
   double4 pf_pos = make_double4(0, 0, 0, 0);
-  bool prev_moved = false;  // the previous step moved particle sgeo.j
-  int prev_j = -1;          // (in every thread) the previous step's particle
+  // the two previous steps (every thread): moved, particle; warp 0 lanes
+  // 0..2 also keep their r' components.  The accept of a step can still be
+  // running in other CTAs when this CTA reads ahead (see the split barrier
+  // below), so loads made one step ahead are checked against both.
+  bool mv1 = false, mv2 = false;
+  int j1 = -1, j2 = -1;
+  double rn1 = 0.0, rn2 = 0.0;
+  // target count of the split barrier that ended the previous step's accept
+  // (0: none pending); reads of state the accept writes wait for it
+  unsigned long long pend = 0;
 
   for (long long t = 0; t < rp.nsteps; t++) {
     const int buf = (int)(t & 1);
@@ -226,10 +239,6 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
           d = pf_d;
           uu = pf_u;
           pj = pf_pos;
-          // the load was issued before the previous step's accept: if that
-          // step moved this particle, its position is the previous r'
-          if (prev_moved && j == sgeo.j && lane < 3)
-            pj = make_double4(sgeo.rn[0], sgeo.rn[1], sgeo.rn[2], sgeo.q);
         } else {
           mc_proposal_axis(rp.seed, (unsigned long long)(rp.step0 + t), rp.chain, S.n, rp.h,
                            lane < 3 ? lane : 0, &j, &d, lane == 3 ? &uu : nullptr);
@@ -238,6 +247,16 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
         if (lane < 3) {
           q = pj.w;
           r = lane == 0 ? pj.x : (lane == 1 ? pj.y : pj.z);
+          // a prefetched load may predate the accept of one of the two
+          // previous steps: if one of them moved this particle, the latest
+          // such r' is its position
+          if (pf_ok) {
+            if (mv1 && j == j1) {
+              r = rn1;
+            } else if (mv2 && j == j2) {
+              r = rn2;
+            }
+          }
           double x = __dadd_rn(r, d);
           if (pbc) {
             if (x < 0.0) x = __dadd_rn(x, S.a);
@@ -341,23 +360,29 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
       nDs += sp_items[l];
       if (S.lev_n[l] > 4) nLB += lev_items[l];
     }
+    // (staged slots by step parity, small-level deltas in three rotating
+    // buffers: the accept of the previous step may still read its own)
+    const int nlev = L - S.lmin + 1;
     auto dslot = [&](int l, int slot) -> double* {
-      return S.dacc + ((size_t)(L - l) * MC_DSLOTS + slot) * C;
+      return S.dacc + (((size_t)(t & 1) * nlev + (L - l)) * MC_DSLOTS + slot) * C;
     };
     const size_t nsC = (size_t)S.nsmall * C;
-    double* dsm = S.dsmall + (size_t)(t & 1) * nsC;             // this step's
-    double* dsm_next = S.dsmall + (size_t)((t + 1) & 1) * nsC;  // zeroed now
+    double* dsm = S.dsmall + (size_t)(t % 3) * nsC;             // this step's
+    double* dsm_next = S.dsmall + (size_t)((t + 1) % 3) * nsC;  // zeroed now
+    // wait of one warp for the previous step's accept (all CTAs)
+    auto need_state = [&]() {
+      if (pend) warp_wait(S.bar, pend, S.status, rp.wait_ns);
+    };
 
     // ------------------------------------- phase A: propose (+ accept deltas)
-    const int nE = L - S.lmin + 1;
     const int nN = same ? 27 : 54;
-    const int iE = nF, iN = nF + nE, iX = nF + nE + nN, iU = iX + 1, iK = iU + 1;
     // K: the far-field change dK of the next proposal, which depends on
     // positions only, is formed one step ahead; this step's far items use
     // the one formed in the previous step unless that step moved the
     // particle this proposal picks
     const bool k_next = pbc && rp.mode == 0 && t + 1 < rp.nsteps;
-    const bool dk_pre = pbc && rp.mode == 0 && t > 0 && !(prev_moved && g.j == prev_j);
+    const bool dk_pre = pbc && rp.mode == 0 && t > 0 && !(mv1 && g.j == j1) && !(mv2 && g.j == j2);
+    const int iF = 0, iE = nF, iN = iE + nE, iX = iN + nN, iU = iX + 1, iK = iU + 1;
     const int nProp = k_next ? iK + 1 : iU + 1;
     const int nPhaseA = nProp + ((spec && !idle) ? nDs : 0);
     double* part = S.partials + buf * MC_MAX_ITEMS;
@@ -393,20 +418,11 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
             }
           }
           double* Dt = dsm + (size_t)(S.lev_off[l] + (se.t3[0] * nl + se.t3[1]) * nl + se.t3[2]) * C;
-          // FP32 evaluation: when alpha = alpha' on this level both sides of
-          // an entry hit the same target, so they are summed in the warp
-          // first (half the L2 atomics; in FP64 the adds would cost more)
-          const bool comb = sizeof(TE) == 4 && co[0] == cn[0] && co[1] == cn[1] && co[2] == cn[2];
           irregular_group_s<TE>(&tabs, p, dx, dy, dz, f, [&](int t2, int n, int m, bool v, TE vr, TE vi) {
-            TE cr = vr, ci = vi;
-            if (comb) {
-              cr += __shfl_xor_sync(0xffffffffu, vr, 8);
-              ci += __shfl_xor_sync(0xffffffffu, vi, 8);
-            }
-            if (se.valid && v && !(comb && side)) {
+            if (se.valid && v) {
               const int kk = rl_re(n, m);
-              atomicAdd(&Dt[kk], to_double(cr));
-              if (m) atomicAdd(&Dt[kk + 1], to_double(neg_bits(ci)));
+              atomicAdd(&Dt[kk], to_double(vr));
+              if (m) atomicAdd(&Dt[kk + 1], to_double(neg_bits(vi)));
             }
           });
         } else {
@@ -463,16 +479,103 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
         for (size_t zi = z0 + lane; zi < z1; zi += 32) __stcg(&dsm_next[zi], 0.0);
       }
       double partial = 0.0;
-      if (idle) {
+      if (k_next && it == iK) {
+        // ---- K: dK of the next proposal (drawn and moved exactly as the
+        //         proposal code of the next step does); runs on idle steps too
+        ptype = 2;
+        int jn;
+        double dn = 0.0;
+        mc_proposal_axis(rp.seed, (unsigned long long)(rp.step0 + t + 1), rp.chain, S.n, rp.h,
+                         lane < 3 ? lane : 0, &jn, &dn, nullptr);
+        const double4 pj = ldcg4(&S.ppos[jn]);
+        double x0 = 0.0, x1 = 0.0;
+        if (lane < 3) {
+          x0 = lane == 0 ? pj.x : (lane == 1 ? pj.y : pj.z);
+          double x = __dadd_rn(x0, dn);
+          if (x < 0.0) x = __dadd_rn(x, S.a);
+          if (x >= S.a) x = __dsub_rn(x, S.a);
+          x1 = x;
+        }
+        const int grp = lane >> 3, side = grp & 1;
+        const double c1 = 0.5 * S.a;
+        double xs[3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ax++) {
+          const double a0 = __shfl_sync(0xffffffffu, x0, ax), a1 = __shfl_sync(0xffffffffu, x1, ax);
+          xs[ax] = side ? a1 : a0;
+        }
+        const TE dx = from_double<TE>(xs[0] - c1), dy = from_double<TE>(xs[1] - c1),
+                 dz = from_double<TE>(xs[2] - c1);
+        double* dst = S.dKpre + (size_t)((t + 1) & 1) * C;
+        regular_group_s<TE>(&tabs, p, dx, dy, dz, from_double<TE>(pj.w),
+                            [&](int t2, int n, int m, bool v, TE vr, TE vi) {
+                              const TE nr = __shfl_xor_sync(0xffffffffu, vr, 8);
+                              const TE ni = __shfl_xor_sync(0xffffffffu, vi, 8);
+                              if (grp == 0 && v) {
+                                const int kk = rl_re(n, m);
+                                __stcg(&dst[kk], to_double(nr - vr));
+                                if (m) __stcg(&dst[kk + 1], to_double(vi - ni));
+                              }
+                            });
+      } else if (idle) {
         // no work: dE is 0 (no move) or +inf (left a free-space box)
         if (it == iX && g.outside) partial = kInf;
         if (it == iU && lane == 0 && rp.mode == 0) part[MC_MAX_ITEMS - 1] = log(u);
         ptype = 3;
-      } else if (it < nF) {
+      } else if (it >= iE && it < iN) {
+        // ---- E: Eq. (2) at r (group 0) and r' (group 1) on level l
+        ptype = 0;
+        const int l = L - (it - iE), sh = L - l;
+        const int grp = lane >> 3, side = grp & 1;
+        const int* cc = side ? g.cfn : g.cf;
+        const int cx = cc[0] >> sh, cy = cc[1] >> sh, cz = cc[2] >> sh;
+        const int nl = S.lev_n[l];
+        const double* Lb = S.Lhat + (size_t)(S.lev_off[l] + (cx * nl + cy) * nl + cz) * C;
+        const TE dx = from_double<TE>(s_off[side][l][0]), dy = from_double<TE>(s_off[side][l][1]),
+                 dz = from_double<TE>(s_off[side][l][2]);
+        // the column polynomials first (positions only), then the
+        // expansion, which the previous accept may still be writing: each
+        // lane contracts its two columns, then applies their diagonal values
+        TE qsv[MC_PMAX + 2];
+        TE D1r, D1i, D2r, D2i;
+        regular_group_q<TE>(&tabs, p, dx, dy, dz, &D1r, &D1i, &D2r, &D2i,
+                            [&](int t2, int n, int m, bool v, bool c1, TE qv) {
+                              qsv[t2] = v ? qv : TE(0);
+                            });
+        need_state();
+        double ld[MC_PMAX + 2], lid[MC_PMAX + 2];
+#pragma unroll
+        for (int t2 = 0; t2 <= MC_PMAX + 1; t2++) {
+          int n, m;
+          bool v;
+          group_nm(p, t2, &n, &m, &v);
+          const int k = rl_re(n, m);
+          ld[t2] = v ? __ldcg(&Lb[k]) : 0.0;
+          lid[t2] = (v && m) ? __ldcg(&Lb[k + 1]) : 0.0;
+        }
+        const int m1 = lane & 7, len1 = p - m1 + 1;
+        TE SR = TE(0), SI = TE(0), SR1 = TE(0), SI1 = TE(0);
+#pragma unroll
+        for (int t2 = 0; t2 <= MC_PMAX + 1; t2++) {
+          if (t2 <= p + 1) {
+            const bool sw = t2 == len1;  // first step of column 2
+            SR1 = sw ? SR : SR1;
+            SI1 = sw ? SI : SI1;
+            SR = sw ? TE(0) : SR;
+            SI = sw ? TE(0) : SI;
+            SR += from_double<TE>(ld[t2]) * qsv[t2];
+            SI += from_double<TE>(lid[t2]) * qsv[t2];
+          }
+        }
+        TE acc = (m1 ? TE(2) : TE(1)) * (D1r * SR1 - D1i * SI1) + TE(2) * (D2r * SR - D2i * SI);
+        acc = group_sum(acc);
+        const TE accn = __shfl_sync(0xffffffffu, acc, 8);
+        partial = g.q * to_double(accn - acc);
+      } else if (it < iE) {
         // ---- F: far lattice, Sec. 3.3 (iv) in the factored form
         //   dU_inf = sum_k W_k dK_k (H_k + 1/2 (G dK)_k),  W = 1 (m = 0) or 2
         ptype = 2;
-        const int f = it;
+        const int f = it - iF;
         const int rb = f / nfc, cb = f % nfc;
         const double c1 = 0.5 * S.a;
         double* st = stage[warp];
@@ -480,6 +583,7 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
         const int grp = lane >> 3;
         const double* xg = (grp & 1) ? g.rn : g.r;
         const int k = rb * 32 + lane;
+        need_state();
         const double hk = (cb == 0 && k < C) ? __ldcg(&S.Hhat[k]) : 0.0;
         if (dk_pre) {
           const double* src = S.dKpre + (size_t)(t & 1) * C;
@@ -519,53 +623,6 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
         }
         partial = warp_sum(contrib);
         __syncwarp();
-      } else if (it < iN) {
-        // ---- E: Eq. (2) at r (group 0) and r' (group 1) on level l
-        ptype = 0;
-        const int l = L - (it - iE), sh = L - l;
-        const int grp = lane >> 3, side = grp & 1;
-        const int* cc = side ? g.cfn : g.cf;
-        const int cx = cc[0] >> sh, cy = cc[1] >> sh, cz = cc[2] >> sh;
-        const int nl = S.lev_n[l];
-        const double* Lb = S.Lhat + (size_t)(S.lev_off[l] + (cx * nl + cy) * nl + cz) * C;
-        double ld[MC_PMAX + 2], lid[MC_PMAX + 2];
-#pragma unroll
-        for (int t2 = 0; t2 <= MC_PMAX + 1; t2++) {
-          int n, m;
-          bool v;
-          group_nm(p, t2, &n, &m, &v);
-          const int k = rl_re(n, m);
-          ld[t2] = v ? __ldcg(&Lb[k]) : 0.0;
-          lid[t2] = (v && m) ? __ldcg(&Lb[k + 1]) : 0.0;
-        }
-        TE Lr[MC_PMAX + 2], Li[MC_PMAX + 2];
-#pragma unroll
-        for (int t2 = 0; t2 <= MC_PMAX + 1; t2++) {
-          Lr[t2] = from_double<TE>(ld[t2]);
-          Li[t2] = from_double<TE>(lid[t2]);
-        }
-        const TE dx = from_double<TE>(s_off[side][l][0]), dy = from_double<TE>(s_off[side][l][1]),
-                 dz = from_double<TE>(s_off[side][l][2]);
-        // each lane contracts its two columns with the real column
-        // polynomials, then applies their diagonal values
-        const int m1 = lane & 7, len1 = p - m1 + 1;
-        TE SR = TE(0), SI = TE(0), SR1 = TE(0), SI1 = TE(0);
-        TE D1r, D1i, D2r, D2i;
-        regular_group_q<TE>(&tabs, p, dx, dy, dz, &D1r, &D1i, &D2r, &D2i,
-                            [&](int t2, int n, int m, bool v, bool c1, TE qv) {
-                              const bool sw = t2 == len1;  // first step of column 2
-                              SR1 = sw ? SR : SR1;
-                              SI1 = sw ? SI : SI1;
-                              SR = sw ? TE(0) : SR;
-                              SI = sw ? TE(0) : SI;
-                              const TE qs = v ? qv : TE(0);
-                              SR += Lr[t2] * qs;
-                              SI += Li[t2] * qs;
-                            });
-        TE acc = (m1 ? TE(2) : TE(1)) * (D1r * SR1 - D1i * SI1) + TE(2) * (D2r * SR - D2i * SI);
-        acc = group_sum(acc);
-        const TE accn = __shfl_sync(0xffffffffu, acc, 8);
-        partial = g.q * to_double(accn - acc);
       } else if (it < iX) {
         // ---- N: Alg. 1 over one near cell (27 cells of the extended domain)
         ptype = 1;
@@ -591,6 +648,7 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
           c1 = e1;
           c2 = e2;
         }
+        need_state();
         if (valid) {
           const int cell = (c0 * nL + c1) * nL + c2;
           const int cnt = __ldcg(&S.ccount[cell]);
@@ -677,6 +735,7 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
         if (pbc) {
           partial += g.q * g.q / S.a * kImageConst;
           if (S.dip == 0) {
+            need_state();
             const double cdip = -2.0 * kPi / (3.0 * S.V);
             double D2 = 0.0, Dn2 = 0.0;
 #pragma unroll
@@ -693,44 +752,6 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
         // ---- U: log(u) for the Metropolis test
         ptype = 3;
         if (lane == 0 && rp.mode == 0) part[MC_MAX_ITEMS - 1] = log(u);
-      } else {
-        // ---- K: dK of the next proposal (drawn and moved exactly as the
-        //         proposal code of the next step does)
-        ptype = 2;
-        int jn;
-        double dn = 0.0;
-        mc_proposal_axis(rp.seed, (unsigned long long)(rp.step0 + t + 1), rp.chain, S.n, rp.h,
-                         lane < 3 ? lane : 0, &jn, &dn, nullptr);
-        const double4 pj = ldcg4(&S.ppos[jn]);
-        double x0 = 0.0, x1 = 0.0;
-        if (lane < 3) {
-          x0 = lane == 0 ? pj.x : (lane == 1 ? pj.y : pj.z);
-          double x = __dadd_rn(x0, dn);
-          if (x < 0.0) x = __dadd_rn(x, S.a);
-          if (x >= S.a) x = __dsub_rn(x, S.a);
-          x1 = x;
-        }
-        const int grp = lane >> 3, side = grp & 1;
-        const double c1 = 0.5 * S.a;
-        double xs[3];
-#pragma unroll
-        for (int ax = 0; ax < 3; ax++) {
-          const double a0 = __shfl_sync(0xffffffffu, x0, ax), a1 = __shfl_sync(0xffffffffu, x1, ax);
-          xs[ax] = side ? a1 : a0;
-        }
-        const TE dx = from_double<TE>(xs[0] - c1), dy = from_double<TE>(xs[1] - c1),
-                 dz = from_double<TE>(xs[2] - c1);
-        double* dst = S.dKpre + (size_t)((t + 1) & 1) * C;
-        regular_group_s<TE>(&tabs, p, dx, dy, dz, from_double<TE>(pj.w),
-                            [&](int t2, int n, int m, bool v, TE vr, TE vi) {
-                              const TE nr = __shfl_xor_sync(0xffffffffu, vr, 8);
-                              const TE ni = __shfl_xor_sync(0xffffffffu, vi, 8);
-                              if (grp == 0 && v) {
-                                const int kk = rl_re(n, m);
-                                __stcg(&dst[kk], to_double(nr - vr));
-                                if (m) __stcg(&dst[kk + 1], to_double(vi - ni));
-                              }
-                            });
       }
       if (lane == 0) part[it] = partial;
       if (prof_on && lane == 0) prof_item(rp.prof, ptype, t_item);
@@ -742,6 +763,7 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
     }
     gen++;
     if (!grid_barrier(S.bar, gen * (unsigned long long)(nCTA + rp.bar_missing), S.status, rp.wait_ns)) break;
+    pend = 0;  // the full barrier covers the previous accept
     if (prof_lead) {
       tp0 = mc_globaltimer();
       rp.prof[1] += tp0 - tp1;
@@ -795,8 +817,12 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
       rp.prof[2] += tp1 - tp0;
       rp.prof[5] += 1;
     }
-    prev_moved = accept && !nomove;
-    prev_j = g.j;
+    mv2 = mv1;
+    j2 = j1;
+    rn2 = rn1;
+    mv1 = accept && !nomove;
+    j1 = g.j;
+    if (warp == 0 && lane < 3) rn1 = g.rn[lane];
     if (!accept || nomove) {
       if (accept) n_acc++;
       if (accept && cta == 0 && threadIdx.x == 0) S.energy[0] += dE_used;
@@ -970,19 +996,11 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
           }
         }
         double* Lt = S.Lhat + (size_t)(S.lev_off[l] + (se.t3[0] * nl + se.t3[1]) * nl + se.t3[2]) * C;
-        // FP32 evaluation: both sides of an entry summed in the warp when
-        // alpha = alpha' on this level (same target)
-        const bool comb = sizeof(TE) == 4 && co[0] == cn[0] && co[1] == cn[1] && co[2] == cn[2];
         irregular_group_s<TE>(&tabs, p, dx, dy, dz, f, [&](int t2, int n, int m, bool v, TE vr, TE vi) {
-          TE cr = vr, ci = vi;
-          if (comb) {
-            cr += __shfl_xor_sync(0xffffffffu, vr, 8);
-            ci += __shfl_xor_sync(0xffffffffu, vi, 8);
-          }
-          if (se.valid && v && !(comb && side)) {
+          if (se.valid && v) {
             const int kk = rl_re(n, m);
-            atomicAdd(&Lt[kk], to_double(cr));
-            if (m) atomicAdd(&Lt[kk + 1], to_double(neg_bits(ci)));
+            atomicAdd(&Lt[kk], to_double(vr));
+            if (m) atomicAdd(&Lt[kk + 1], to_double(neg_bits(vi)));
           }
         });
         if (prof_on && lane == 0) prof_item(rp.prof, 4, t_item);
@@ -1049,8 +1067,11 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
       rp.prof[3] += tp0 - tp1;
       rp.prof[6] += 1;
     }
+    // split barrier: arrive and go on with the next proposal; its reads of
+    // the state written above wait for the count (need_state)
     gen++;
-    if (!grid_barrier(S.bar, gen * (unsigned long long)(nCTA + rp.bar_missing), S.status, rp.wait_ns)) break;
+    grid_arrive(S.bar);
+    pend = gen * (unsigned long long)(nCTA + rp.bar_missing);
     if (prof_lead) rp.prof[4] += mc_globaltimer() - tp0;
     if (rp.stop_after_accepts > 0 && n_acc >= rp.stop_after_accepts) break;
   }

@@ -69,7 +69,7 @@ struct McSys {
   int nsmall;        // cells of levels lmin .. ls_end-1 (the first cells of Lhat)
   unsigned long long* sync;  // [16]: [l] read epoch of level l, [12] near items done
   // speculative accept: Alg. L.2 contributions staged during the proposal
-  double* dacc;      // [(L - lmin + 1) * MC_DSLOTS * C]
+  double* dacc;      // [2 (step parity) * (L - lmin + 1) * MC_DSLOTS * C]
   double* dKpre;     // [2 * C] dK of the next proposal, by step parity
 };
 
@@ -231,6 +231,47 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* ctr, unsigned l
   return s_ok != 0;
 }
 
+// Split grid barrier: arrive (release) without waiting ...
+__device__ __forceinline__ void grid_arrive(unsigned long long* ctr) {
+  __syncthreads();
+  if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(ctr) : "memory");
+}
+
+// ... and a wait of one warp for a target count (lane 0 polls, bounded by
+// wait_ns; acquire once the count is reached); false on timeout or when
+// another CTA has set an error status
+__device__ __forceinline__ bool warp_wait(unsigned long long* ctr, unsigned long long target,
+                                          int* status, long long wait_ns) {
+  int ok = 1;
+  if ((threadIdx.x & 31) == 0) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
+    if (v < target) {
+      const unsigned long long t0 = mc_globaltimer();
+      unsigned spins = 0;
+      while (true) {
+        asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
+        if (v >= target) break;
+        if ((++spins & 63u) == 0u) {
+          if ((long long)(mc_globaltimer() - t0) > wait_ns) {
+            atomicExch(status, MCD_ERR_TIMEOUT);
+            ok = 0;
+            break;
+          }
+          if (*((volatile int*)status) != MCD_OK) {
+            ok = 0;
+            break;
+          }
+        }
+      }
+    }
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+  }
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  __syncwarp();
+  return ok != 0;
+}
+
 // ------------------------------------------------------ recurrence tables
 template <typename T>
 struct HarmTabs {
@@ -324,7 +365,7 @@ __device__ __forceinline__ void cmul(T ar, T ai, T br, T bi, T* cr, T* ci) {
   *ci = ar * bi + ai * br;
 }
 
-template <typename T, typename F>
+template <typename T, typename F, bool kUnroll = true>
 __device__ __forceinline__ void harm_group(const T (*A)[16], const T (*B)[16], int p, T X, T Y,
                                            T Z, T Q, T start, F&& use) {
   const int g = threadIdx.x & 7;
@@ -368,26 +409,33 @@ __device__ __forceinline__ void harm_group(const T (*A)[16], const T (*B)[16], i
   const T d2r = (m2c & 1) ? o2r : e2r, d2i = (m2c & 1) ? o2i : e2i;
   const int len1 = p - m1 + 1;
   T p1r = T(0), p1i = T(0), p2r = T(0), p2i = T(0);
+  auto step = [&](int t) {
+    const bool c1 = t < len1;
+    const int m = c1 ? m1 : m2c;
+    const int n = c1 ? (m1 + t) : (m2c + t - len1);
+    const bool valid = active && (c1 || two) && n <= p;
+    const bool st = (n == m);
+    const int nn = n > 15 ? 15 : n;
+    const T a = Z * A[nn][m], b = Q * B[nn][m];
+    T vr = a * p1r - b * p2r, vi = a * p1i - b * p2i;
+    const T sr = c1 ? d1r : d2r, si = c1 ? d1i : d2i;
+    vr = st ? sr : vr;
+    vi = st ? si : vi;
+    p2r = st ? T(0) : p1r;
+    p2i = st ? T(0) : p1i;
+    p1r = vr;
+    p1i = vi;
+    use(t, n, m, valid, vr, vi);
+  };
+  if constexpr (kUnroll) {
+    // consumers that keep per-step values in register arrays need t constant
 #pragma unroll
-  for (int t = 0; t <= MC_PMAX + 1; t++) {
-    if (t <= p + 1) {
-      const bool c1 = t < len1;
-      const int m = c1 ? m1 : m2c;
-      const int n = c1 ? (m1 + t) : (m2c + t - len1);
-      const bool valid = active && (c1 || two) && n <= p;
-      const bool st = (n == m);
-      const int nn = n > 15 ? 15 : n;
-      const T a = Z * A[nn][m], b = Q * B[nn][m];
-      T vr = a * p1r - b * p2r, vi = a * p1i - b * p2i;
-      const T sr = c1 ? d1r : d2r, si = c1 ? d1i : d2i;
-      vr = st ? sr : vr;
-      vi = st ? si : vi;
-      p2r = st ? T(0) : p1r;
-      p2i = st ? T(0) : p1i;
-      p1r = vr;
-      p1i = vi;
-      use(t, n, m, valid, vr, vi);
-    }
+    for (int t = 0; t <= MC_PMAX + 1; t++)
+      if (t <= p + 1) step(t);
+  } else {
+    // a rolled loop: much less code where every step writes memory
+#pragma unroll 1
+    for (int t = 0; t <= p + 1; t++) step(t);
   }
 }
 
@@ -425,12 +473,13 @@ __device__ __forceinline__ void irregular_group(const HarmTabs<T>* t, int p, T x
 }
 
 // The same sets times a factor s (the recurrence is linear in its start
-// value, so the factor costs one multiply instead of one per coefficient).
+// value, so the factor costs one multiply instead of one per coefficient),
+// with a rolled step loop (use() sees a run-time t).
 template <typename T, typename F>
 __device__ __forceinline__ void regular_group_s(const HarmTabs<T>* t, int p, T x, T y, T z, T s,
                                                 F&& use) {
   const T r2 = x * x + y * y + z * z;
-  harm_group<T>(t->rA, t->rB, p, x, y, z, r2, s, use);
+  harm_group<T, F, false>(t->rA, t->rB, p, x, y, z, r2, s, static_cast<F&&>(use));
 }
 
 template <typename T, typename F>
@@ -439,7 +488,7 @@ __device__ __forceinline__ void irregular_group_s(const HarmTabs<T>* t, int p, T
   const T r2 = x * x + y * y + z * z;
   const T ir = mc_rsqrt(r2);
   const T ir2 = ir * ir;
-  harm_group<T>(t->iA, t->iB, p, x * ir2, y * ir2, z * ir2, ir2, ir * s, use);
+  harm_group<T, F, false>(t->iA, t->iB, p, x * ir2, y * ir2, z * ir2, ir2, ir * s, static_cast<F&&>(use));
 }
 
 // Column factorisation: every scaled harmonic of column m is the diagonal
