@@ -139,9 +139,9 @@ int mc_lattice_sums(int lmax, double *out);
  *                          Legendre-series corrections.  Same results to
  *                          roundoff; slower on GB300 in the measurements so
  *                          far (contention of the merged phase);
- *   MC_SCHEDULE_PLAIN      (default for batches) as PHASED, with the Alg. L.2
- *                          contributions computed after the decision (no
- *                          work on rejected moves). */
+ *   MC_SCHEDULE_PLAIN      (default for FP32-eval batches) as PHASED, with
+ *                          the Alg. L.2 contributions computed after the
+ *                          decision (no work on rejected moves). */
 #define MC_SCHEDULE_PHASED 0
 #define MC_SCHEDULE_PIPELINED 1
 #define MC_SCHEDULE_PLAIN 2
@@ -201,7 +201,8 @@ int mc_batch_run(mc_batch *b, int64_t n_steps, const uint64_t *seeds, double bet
                  uint8_t *log_acc);
 /* CTAs given to each chain (n_chains ints) and the far-field tile count. */
 int mc_batch_info(mc_batch *b, int *ctas_out, int *nf_cols_out);
-/* Schedule of the batch's chains (MC_SCHEDULE_*, default plain). */
+/* Schedule of the batch's chains (MC_SCHEDULE_*; default phased for FP64,
+ * plain for FP32-eval batches). */
 int mc_batch_set_schedule(mc_batch *b, int schedule);
 void mc_batch_destroy(mc_batch *b);
 

@@ -25,8 +25,8 @@ cudaError_t mc_launch_batch_pipe(const McSys* const* d_systems, RunParams* d_rps
                                  const int* d_cta_chain, const int* d_cta_rank,
                                  const int* d_chain_ctas, int prec, int nCTA, cudaStream_t stream);
 cudaError_t mc_launch_batch(const McSys* const* d_systems, RunParams* d_rps, const int* d_cta_chain,
-                            const int* d_cta_rank, const int* d_chain_ctas, int prec, int nCTA,
-                            cudaStream_t stream);
+                            const int* d_cta_rank, const int* d_chain_ctas, int prec, int spec,
+                            int nCTA, cudaStream_t stream);
 int mc_chain_max_ctas(int prec);
 __global__ void k_cell_count(int, const double4*, double, int, int*, int*);
 __global__ void k_cell_fill(int, const int*, int, int*, int*);
@@ -875,7 +875,7 @@ int batch_enqueue(mc_batch* b) {
                             b->d_chain_ctas, b->prec, b->nCTA, b->stream));
   } else {
     CK(mc_launch_batch(b->d_systems, b->d_rps, b->d_cta_chain, b->d_cta_rank, b->d_chain_ctas,
-                       b->prec, b->nCTA, b->stream));
+                       b->prec, b->schedule == MC_SCHEDULE_PHASED ? 1 : 0, b->nCTA, b->stream));
   }
   return MC_OK;
 }
@@ -932,7 +932,9 @@ int mc_batch_create(mc_batch** out, int n_chains, mc_ctx* const* ctxs) {
     return MC_ERR_ARG;  // every chain needs at least one CTA
   }
   b->nf_cols = 4;
-  b->schedule = MC_SCHEDULE_PLAIN;
+  // measured on GB300 (64 chains, p = 10): speculation pays in FP64, where
+  // each item is long, and costs in the FP32-eval form
+  b->schedule = b->prec == MC_FP64 ? MC_SCHEDULE_PHASED : MC_SCHEDULE_PLAIN;
   std::vector<double> w(n_chains);
   for (int i = 0; i < n_chains; i++) w[i] = (double)(ctxs[i]->h.L - ctxs[i]->h.lmin + 1);
   b->ctas = split_by_weight(w, b->sms);

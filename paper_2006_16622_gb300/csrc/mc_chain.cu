@@ -142,7 +142,10 @@ __device__ __forceinline__ SmallEntry small_entry(const unsigned short (*il)[189
   return se;
 }
 
-template <typename TE>
+// kSpec: speculative accept (MC_SCHEDULE_PHASED) or accept computed after the
+// decision (MC_SCHEDULE_PLAIN), as separate instantiations (smaller code per
+// kernel: the instruction cache is a measured limit of this kernel)
+template <typename TE, bool kSpec>
 __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunParams& rp,
                                            const int nCTA, const int cta) {
   __shared__ McSys S;
@@ -174,7 +177,7 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
   const bool pbc = (S.bc == 0);
   const int nWarpsTot = nCTA * MC_WARPS;
   const int gw = warp * nCTA + cta;  // this warp's first item of every phase
-  const bool spec = rp.spec != 0;
+  constexpr bool spec = kSpec;
   unsigned long long gen = 0;
   long long n_acc = 0, n_border = 0, steps_done = 0;
   const bool prof_on = rp.prof != nullptr;
@@ -1084,10 +1087,10 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
 }
 
 // one chain on the whole grid
-template <typename TE>
+template <typename TE, bool kSpec>
 __global__ void __launch_bounds__(MC_THREADS, 1)
     mc_chain_kernel(const McSys* __restrict__ sysp, RunParams rp) {
-  chain_body<TE>(sysp, rp, (int)gridDim.x, (int)blockIdx.x);
+  chain_body<TE, kSpec>(sysp, rp, (int)gridDim.x, (int)blockIdx.x);
 }
 
 // many independent chains: CTA b runs chain cta_chain[b] as rank cta_rank[b]
@@ -1095,7 +1098,7 @@ __global__ void __launch_bounds__(MC_THREADS, 1)
 // barrier counter, partials and status in its McSys); per-chain parameters
 // in device memory, step counter advanced in place so that a replayed graph
 // continues every chain's proposal stream
-template <typename TE>
+template <typename TE, bool kSpec>
 __global__ void __launch_bounds__(MC_THREADS, 1)
     mc_batch_kernel(const McSys* const* __restrict__ systems, RunParams* __restrict__ rps,
                     const int* __restrict__ cta_chain, const int* __restrict__ cta_rank,
@@ -1103,7 +1106,7 @@ __global__ void __launch_bounds__(MC_THREADS, 1)
   const int ch = cta_chain[blockIdx.x];
   RunParams rp = rps[ch];
   const McSys* sys = systems[ch];
-  chain_body<TE>(sys, rp, chain_ctas[ch], cta_rank[blockIdx.x]);
+  chain_body<TE, kSpec>(sys, rp, chain_ctas[ch], cta_rank[blockIdx.x]);
   if (cta_rank[blockIdx.x] == 0 && threadIdx.x == 0) {
     // every CTA of the group read rps[ch] before the group's first barrier
     const long long done = sys->stats[0];
@@ -1111,24 +1114,25 @@ __global__ void __launch_bounds__(MC_THREADS, 1)
   }
 }
 
-template __global__ void mc_chain_kernel<double>(const McSys*, RunParams);
-template __global__ void mc_chain_kernel<float>(const McSys*, RunParams);
-template __global__ void mc_batch_kernel<double>(const McSys* const*, RunParams*, const int*,
-                                                 const int*, const int*);
-template __global__ void mc_batch_kernel<float>(const McSys* const*, RunParams*, const int*,
-                                                const int*, const int*);
+template __global__ void mc_chain_kernel<double, true>(const McSys*, RunParams);
+template __global__ void mc_chain_kernel<float, true>(const McSys*, RunParams);
+template __global__ void mc_chain_kernel<double, false>(const McSys*, RunParams);
+template __global__ void mc_chain_kernel<float, false>(const McSys*, RunParams);
 
 // host-side launchers (cooperative launches: all CTAs co-resident)
 cudaError_t mc_launch_chain(const McSys* d_sys, const RunParams& rp, int prec, int nCTA,
                             cudaStream_t stream) {
   void* args[] = {(void*)&d_sys, (void*)&rp};
-  const void* fn = prec ? (const void*)mc_chain_kernel<float> : (const void*)mc_chain_kernel<double>;
+  const void* fn = rp.spec ? (prec ? (const void*)mc_chain_kernel<float, true>
+                                   : (const void*)mc_chain_kernel<double, true>)
+                           : (prec ? (const void*)mc_chain_kernel<float, false>
+                                   : (const void*)mc_chain_kernel<double, false>);
   return cudaLaunchCooperativeKernel(fn, dim3(nCTA), dim3(MC_THREADS), args, 0, stream);
 }
 
 cudaError_t mc_launch_batch(const McSys* const* d_systems, RunParams* d_rps, const int* d_cta_chain,
-                            const int* d_cta_rank, const int* d_chain_ctas, int prec, int nCTA,
-                            cudaStream_t stream) {
+                            const int* d_cta_rank, const int* d_chain_ctas, int prec, int spec,
+                            int nCTA, cudaStream_t stream) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nCTA);
   cfg.blockDim = dim3(MC_THREADS);
@@ -1139,10 +1143,16 @@ cudaError_t mc_launch_batch(const McSys* const* d_systems, RunParams* d_rps, con
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (prec)
-    return cudaLaunchKernelEx(&cfg, mc_batch_kernel<float>, d_systems, d_rps, d_cta_chain,
+  if (prec && spec)
+    return cudaLaunchKernelEx(&cfg, mc_batch_kernel<float, true>, d_systems, d_rps, d_cta_chain,
                               d_cta_rank, d_chain_ctas);
-  return cudaLaunchKernelEx(&cfg, mc_batch_kernel<double>, d_systems, d_rps, d_cta_chain,
+  if (prec)
+    return cudaLaunchKernelEx(&cfg, mc_batch_kernel<float, false>, d_systems, d_rps, d_cta_chain,
+                              d_cta_rank, d_chain_ctas);
+  if (spec)
+    return cudaLaunchKernelEx(&cfg, mc_batch_kernel<double, true>, d_systems, d_rps, d_cta_chain,
+                              d_cta_rank, d_chain_ctas);
+  return cudaLaunchKernelEx(&cfg, mc_batch_kernel<double, false>, d_systems, d_rps, d_cta_chain,
                             d_cta_rank, d_chain_ctas);
 }
 
@@ -1150,7 +1160,8 @@ int mc_chain_max_ctas(int prec) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const void* fn = prec ? (const void*)mc_chain_kernel<float> : (const void*)mc_chain_kernel<double>;
+  const void* fn = prec ? (const void*)mc_chain_kernel<float, true>
+                        : (const void*)mc_chain_kernel<double, true>;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, MC_THREADS, 0);
   if (per < 1) return 0;
   return sms;  // one CTA per SM
