@@ -200,13 +200,14 @@ def bytes_per_step(p, levels, nbar, nu):
 
 
 def read_profile_traffic():
-    """DRAM bytes per MH step of the chain kernel from the committed ncu summary."""
-    path = os.path.join(ROOT, "profiles", "chain_fp64_uniform_N1e5.md")
+    """DRAM bytes per launch of the timed chain kernel (50 000 proposals) from
+    the committed ncu summary of one full launch, or None."""
+    path = os.path.join(ROOT, "profiles", "chain_fp64_dram_full_launch_N1e5.md")
     try:
         for line in open(path):
-            if line.startswith("dram_bytes_per_mh_step:"):
-                return float(line.split(":")[1])
-    except OSError:
+            if line.startswith("dram_bytes_per_launch:"):
+                return float(line.split(":")[1].split()[0])
+    except (OSError, ValueError, IndexError):
         pass
     return None
 
@@ -460,10 +461,10 @@ def gpu_arm(args):
     F, Fp, Fa = algorithmic_flops_per_step(W.p, W.levels, nbar, r64["nu"])
     per_launch = statistics.mean(r64["durs"])
     achieved = F * S / per_launch
-    traffic_per_step = read_profile_traffic()
+    traffic_launch = read_profile_traffic() if S == 50_000 else None
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
             "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_FLOPS,
-            "traffic": (traffic_per_step * S) if traffic_per_step else None,
+            "traffic": traffic_launch,
             "kernel": "mc_chain_kernel<double>",
             "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (recipe unit counts)",
             "flops_per_mh_step": F, "bytes_per_mh_step": bytes_per_step(W.p, W.levels, nbar, r64["nu"]),
