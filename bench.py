@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-huge", action="store_true", help="skip the N=1e6 setup/step leg")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the per-operation timing vs N")
     ap.add_argument("--huge-steps", type=int, default=100_000,
                     help="proposals timed per form on the N=1e6 workload")
     return ap.parse_args()
@@ -308,6 +309,46 @@ def huge_workload_leg(args, stream, flush):
     return out
 
 
+def size_sweep_leg(stream):
+    """Per-operation times against N (density 0.1, ~20 charges per finest
+    cell, p = 12, h = 0.3): MH steps/s of both forms over 20 000 proposals,
+    and from the device timers of CTA 0 the propose phase (proposal draw to
+    the decision's barrier) and the accept phase per accepted move."""
+    import numpy as np
+    import torch
+
+    from paper_2006_16622_gb300 import mcfmm
+    from paper_2006_16622_gb300.workloads import size_sweep
+
+    rows = []
+    for W in size_sweep():
+        pos, q = W.system()
+        row = {"n": W.n, "levels": W.levels, "p": W.p}
+        for prec, name in ((mcfmm.FP64, "fp64"), (mcfmm.FP32_EVAL, "fp32_eval")):
+            ctx = mcfmm.Context(pos, q, W.a, W.levels, W.p, precision=prec, stream=stream.cuda_stream)
+            ctx.setup(mcfmm.SETUP_FMM if W.n >= 1_000_000 else mcfmm.SETUP_P2L)
+            ctx.run(2000, seed=1, beta=W.beta, half_width=W.half_width, stats=False)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.run(20_000, seed=2, beta=W.beta, half_width=W.half_width, stats=False)
+            e1.record(stream)
+            e1.synchronize()
+            row[f"{name}_mh_steps_per_s"] = 20_000 / (e0.elapsed_time(e1) / 1000.0)
+            ctx.profile(True)
+            ctx.profile_read()
+            ctx.run(5000, seed=3, beta=W.beta, half_width=W.half_width, stats=False)
+            pr = ctx.profile_read().astype(np.float64)
+            ctx.profile(False)
+            steps, acc = max(pr[5], 1.0), max(pr[6], 1.0)
+            row[f"{name}_propose_us"] = (pr[0] + pr[1]) / steps / 1e3
+            row[f"{name}_accept_us"] = (pr[3] + pr[4]) / acc / 1e3
+            row[f"{name}_acceptance"] = pr[6] / steps
+            ctx.close()
+        rows.append(row)
+    return rows
+
+
 def precision_form_stats(W, stream):
     """FP32-eval vs the (oracle-parity-tested) FP64 chain on the same seed:
     per-proposal dE error over the common prefix of the two chains, and the
@@ -429,6 +470,7 @@ def gpu_arm(args):
         rb64 = batched_form(args, mcfmm.FP64, stream, flush)
     prec_stats = None if args.no_precision else precision_form_stats(W, stream)
     huge = None if (args.no_huge or rank != 0) else huge_workload_leg(args, stream, flush)
+    sweep = None if (args.no_sweep or rank != 0) else size_sweep_leg(stream)
 
     # end to end through the C ABI: host arrays in, positions and energy out
     e2e = None
@@ -508,7 +550,7 @@ def gpu_arm(args):
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": args.steps, "clocks": r64["clocks"], "forms": forms,
             "precision_form": prec_stats,
-            "setup_s": r64["setup_s"], "huge": huge}
+            "setup_s": r64["setup_s"], "huge": huge, "size_sweep": sweep}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -63,6 +63,8 @@ def lib():
             L.orc_setup.argtypes = [_P]
             L.orc_setup_fmm.argtypes = [_P]
             L.orc_fmm_local_cell.argtypes = [_P, ctypes.c_int, _P, _P]
+            L.orc_setup_multipole.argtypes = [_P]
+            L.orc_get_multipole.argtypes = [_P, ctypes.c_int, _P]
             L.orc_propose.restype = _D
             L.orc_propose.argtypes = [_P, _I64, _P]
             L.orc_last_parts.argtypes = [_P, _P]
@@ -216,6 +218,16 @@ class System:
 
     def setup_fmm(self):
         lib().orc_setup_fmm(self._h)
+
+    def setup_multipole(self):
+        lib().orc_setup_multipole(self._h)
+
+    def multipole(self, level):
+        nl = 1 << (level - 1)
+        out = np.zeros((nl ** 3, self.C))
+        if lib().orc_get_multipole(self._h, level, _ptr(out)) != 0:
+            raise ValueError("bad level or no multipoles")
+        return out
 
     def fmm_local_cell(self, level, c):
         cc = np.ascontiguousarray(np.asarray(c, dtype=np.int32))

@@ -368,6 +368,10 @@ struct orc_sys {
   int *cell_of;
   /* per-level local coefficients L^Delta_{l,alpha}, index [l][cell*C + IDX] */
   cplx *Lx[16];
+  /* multipole method (Sec. 3.2, alternative algorithm): per-level multipole
+   * coefficients M_{l,alpha} of Eq. (4), same indexing; method 1 selects it */
+  int method;
+  cplx *Mx[16];
   /* periodic far field: box multipole K, its conjugate E, lattice sums */
   cplx *K, *E, *Slat;
   double D[3];
@@ -540,6 +544,7 @@ void orc_destroy(orc_sys *s) {
   free(s->cap);
   free(s->cell_of);
   for (int l = 2; l <= s->L; l++) free(s->Lx[l]);
+  for (int l = 2; l <= s->L; l++) free(s->Mx[l]);
   free(s->K);
   free(s->E);
   free(s->Slat);
@@ -673,33 +678,62 @@ static void fmm_target(orc_sys *s, int l, const int bc[3], const cplx *Mlev, cpl
   free(R);
 }
 
-static void setup_local_fmm(orc_sys *s) {
-  int C = s->C, p = s->p;
+/* Eq. (4) about each cell centre of level l, into M (zeroed here); the
+ * loop of Alg. M.3 for one level */
+static void multipoles_level(orc_sys *s, int l, cplx *M) {
+  int C = s->C, p = s->p, nl = ncell_axis(l);
   cplx *R = (cplx *)malloc(sizeof(cplx) * C);
+  memset(M, 0, sizeof(cplx) * (size_t)nl * nl * nl * C);
+  for (int64_t i = 0; i < s->n; i++) {
+    int cf[3], c[3];
+    finest_cell(s, &s->pos[3 * i], cf);
+    for (int d = 0; d < 3; d++) c[d] = cf[d] >> (s->L - l);
+    double Rc[3], d3[3];
+    cell_centre(s, l, c, Rc);
+    for (int t = 0; t < 3; t++) d3[t] = s->pos[3 * i + t] - Rc[t];
+    regular_table(p, d3, R);
+    cplx *Mc = M + (size_t)lin(nl, c) * C;
+    for (int nn = 0; nn <= p; nn++)
+      for (int m = -nn; m <= nn; m++) Mc[IDX(nn, m)] += s->q[i] * R[IDX(nn, -m)];
+  }
+  free(R);
+}
+
+static void setup_local_fmm(orc_sys *s) {
+  int C = s->C;
   for (int l = 2; l <= s->L; l++) {
     int nl = ncell_axis(l);
     size_t ncell = (size_t)nl * nl * nl;
-    cplx *M = (cplx *)calloc(ncell * C, sizeof(cplx));
-    /* Eq. (4) about each cell centre */
-    for (int64_t i = 0; i < s->n; i++) {
-      int cf[3], c[3];
-      finest_cell(s, &s->pos[3 * i], cf);
-      for (int d = 0; d < 3; d++) c[d] = cf[d] >> (s->L - l);
-      double Rc[3], d3[3];
-      cell_centre(s, l, c, Rc);
-      for (int t = 0; t < 3; t++) d3[t] = s->pos[3 * i + t] - Rc[t];
-      regular_table(p, d3, R);
-      cplx *Mc = M + (size_t)lin(nl, c) * C;
-      for (int nn = 0; nn <= p; nn++)
-        for (int m = -nn; m <= nn; m++) Mc[IDX(nn, m)] += s->q[i] * R[IDX(nn, -m)];
-    }
+    cplx *M = (cplx *)malloc(sizeof(cplx) * ncell * C);
+    multipoles_level(s, l, M);
     for (size_t b = 0; b < ncell; b++) {
       int bc[3] = {(int)(b / ((size_t)nl * nl)), (int)((b / nl) % nl), (int)(b % nl)};
       fmm_target(s, l, bc, M, s->Lx[l] + b * C);
     }
     free(M);
   }
-  free(R);
+}
+
+/* Alg. M.3 (the multipole method's initialisation) with the K/E of
+ * Sec. 3.3 (ii); the system then proposes and accepts with Alg. M.1/M.2 */
+void orc_setup_multipole(orc_sys *s) {
+  s->method = 1;
+  for (int l = 2; l <= s->L; l++) {
+    int nl = ncell_axis(l);
+    if (!s->Mx[l]) s->Mx[l] = (cplx *)malloc(sizeof(cplx) * (size_t)nl * nl * nl * s->C);
+    multipoles_level(s, l, s->Mx[l]);
+  }
+  if (s->bc == ORC_BC_PBC) setup_KE(s);
+  s->energy = orc_energy_fresh(s);
+}
+
+/* multipoles of level `level` (real layout of the unscaled M_n^m) */
+int orc_get_multipole(const orc_sys *s, int level, double *out) {
+  if (level < 2 || level > s->L || !s->Mx[level]) return -1;
+  int nl = ncell_axis(level);
+  for (int c = 0; c < nl * nl * nl; c++)
+    to_real_layout(s->p, s->Mx[level] + (size_t)c * s->C, out + (size_t)c * s->C);
+  return 0;
 }
 
 /* one cell's FMM-variant expansion (real layout), all from the particles:
@@ -714,6 +748,7 @@ int orc_fmm_local_cell(orc_sys *s, int l, const int c[3], double *out) {
 }
 
 void orc_setup_fmm(orc_sys *s) {
+  s->method = 0;
   setup_local_fmm(s);
   if (s->bc == ORC_BC_PBC) setup_KE(s);
   s->energy = orc_energy_fresh(s);
@@ -748,6 +783,34 @@ static double psi_level(orc_sys *s, int l, const int c[3], const double x[3]) {
   return eval_local(s->p, s->Lx[l] + (size_t)lin(nl, c) * s->C, d, s->w2);
 }
 
+/* the multipole method's level sum: sum over the interaction list of cell c
+ * of level l of the multipole expansion (the paper's Phi) of each listed
+ * cell (image-shifted centre) at x */
+static double phi_mm_level(orc_sys *s, int l, const int c[3], const double x[3]) {
+  int nl = ncell_axis(l), off[189][3];
+  int nIL = il_offsets(c, off);
+  double acc = 0.0;
+  for (int k = 0; k < nIL; k++) {
+    int e[3] = {c[0] + off[k][0], c[1] + off[k][1], c[2] + off[k][2]}, cc[3], sh[3];
+    if (!wrap_cell(s, nl, e, cc, sh)) continue;
+    double R[3], d[3];
+    cell_centre(s, l, e, R);
+    for (int t = 0; t < 3; t++) d[t] = x[t] - R[t];
+    irregular_table(s->p, d, s->w2);
+    const cplx *M = s->Mx[l] + (size_t)lin(nl, cc) * s->C;
+    cplx v = 0.0;
+    for (int n = 0; n <= s->p; n++)
+      for (int m = -n; m <= n; m++) v += M[IDX(n, m)] * s->w2[IDX(n, m)];
+    acc += creal(v);
+  }
+  return acc;
+}
+
+/* level-l contribution to the potential at x in cell c (either method) */
+static double level_potential(orc_sys *s, int l, const int c[3], const double x[3]) {
+  return s->method ? phi_mm_level(s, l, c, x) : psi_level(s, l, c, x);
+}
+
 /* U^inf = 1/2 sum E_n^m H_n^m.  The paper prints the sum without the 1/2;
  * the pair energy of the far images carries it, so we read the factor as
  * part of the definition (checked against Ewald summation). */
@@ -776,7 +839,7 @@ static double phi_particle(orc_sys *s, int64_t i) {
   double phi = 0.0;
   for (int l = s->L; l >= 2; l--) {
     int c[3] = {cf[0] >> (s->L - l), cf[1] >> (s->L - l), cf[2] >> (s->L - l)};
-    phi += psi_level(s, l, c, x);
+    phi += level_potential(s, l, c, x);
   }
   for (int dx = -1; dx <= 1; dx++)
     for (int dy = -1; dy <= 1; dy++)
@@ -806,6 +869,7 @@ double orc_energy_fresh(orc_sys *s) {
 }
 
 void orc_setup(orc_sys *s) {
+  s->method = 0;
   setup_local(s);
   if (s->bc == ORC_BC_PBC) setup_KE(s);
   s->energy = orc_energy_fresh(s);
@@ -833,7 +897,7 @@ double orc_propose(orc_sys *s, int64_t j, const double rnew[3]) {
       c[t] = cf[t] >> (s->L - l);
       cn[t] = cfn[t] >> (s->L - l);
     }
-    dU_exp += q * (psi_level(s, l, cn, rnew) - psi_level(s, l, c, r));
+    dU_exp += q * (level_potential(s, l, cn, rnew) - level_potential(s, l, c, r));
   }
 
   /* Alg. 1: direct interactions with the 27 near cells (cells of the
@@ -964,7 +1028,25 @@ void orc_accept(orc_sys *s, int64_t j, const double rnew[3], double dE) {
   finest_cell(s, rnew, cfn);
   int C = s->C;
   cplx *irr = s->w1;
-  for (int l = s->L; l >= 2; l--) {
+  /* Alg. M.2: remove the charge from the multipoles of its old cells and
+   * add it to those of its new cells on every level */
+  for (int l = s->L; s->method && l >= 2; l--) {
+    int nl = ncell_axis(l);
+    for (int side = 0; side < 2; side++) {
+      const int *cfs = side ? cfn : cf;
+      const double *x = side ? rnew : r;
+      double sg = side ? q : -q;
+      int c[3] = {cfs[0] >> (s->L - l), cfs[1] >> (s->L - l), cfs[2] >> (s->L - l)};
+      double Rc[3], d[3];
+      cell_centre(s, l, c, Rc);
+      for (int t = 0; t < 3; t++) d[t] = x[t] - Rc[t];
+      regular_table(s->p, d, irr);
+      cplx *Mc = s->Mx[l] + (size_t)lin(nl, c) * C;
+      for (int nn = 0; nn <= s->p; nn++)
+        for (int m = -nn; m <= nn; m++) Mc[IDX(nn, m)] += sg * irr[IDX(nn, -m)];
+    }
+  }
+  for (int l = s->L; !s->method && l >= 2; l--) {
     int nl = ncell_axis(l);
     for (int side = 0; side < 2; side++) {
       const int *cfs = side ? cfn : cf;

@@ -58,6 +58,12 @@ void orc_setup_fmm(orc_sys *s);
 /* one cell's FMM-variant expansion (real layout), source multipoles taken
  * directly from the charges; -1 for a bad level */
 int orc_fmm_local_cell(orc_sys *s, int level, const int c[3], double *out);
+/* the multipole method (Sec. 3.2, alternative algorithm): Alg. M.3 + K/E +
+ * U0; afterwards propose/accept/run/energy follow Alg. M.1/M.2.  orc_setup
+ * or orc_setup_fmm switch back to the local method. */
+void orc_setup_multipole(orc_sys *s);
+/* level multipoles M_n^m (real layout), -1 for a bad level or before setup */
+int orc_get_multipole(const orc_sys *s, int level, double *out);
 double orc_propose(orc_sys *s, int64_t j, const double rnew[3]);  /* Alg. L.1 */
 /* split of the last proposal: [0] expansions, [1] direct (Alg. 1 incl.
  * image correction), [2] far lattice, [3] dipole (tinfoil) term */

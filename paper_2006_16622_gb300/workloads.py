@@ -85,3 +85,17 @@ def batched_systems(n_chains: int = 64, n_lo: int = 1000, n_hi: int = 50000, rho
         levels = max(3, 1 + int(round(math.log(n / per_cell, 8))))
         out.append((n, a, levels, i))
     return out
+
+
+def size_sweep(sizes=(1_000, 10_000, 100_000, 1_000_000), rho: float = 0.1,
+               per_cell: float = 20.0, p: int = 12, half_width: float = 0.3):
+    """Workloads of the per-operation timing against N at fixed density and
+    about `per_cell` charges per finest cell (levels = 1 + round(log8(N /
+    per_cell)), at least 3)."""
+    out = []
+    for n in sizes:
+        a = (n / rho) ** (1.0 / 3.0)
+        levels = max(3, 1 + int(round(np.log(n / per_cell) / np.log(8.0))))
+        out.append(Workload(f"uniform N={n} rho={rho} a={a:.2f} L={levels} p={p} h={half_width}",
+                            n, a, levels, p, 0, half_width))
+    return out

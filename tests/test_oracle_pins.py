@@ -412,3 +412,84 @@ def test_fmm_variant_setup_converges_to_exact_setup_and_direct_sums():
         b.setup_fmm()
         errs.append(abs(b.energy() - Ud) / abs(Ud))
     assert errs[0] > 10 * errs[1] > 100 * errs[2] and errs[2] < 1e-6
+
+
+# ------------------------------------------------ multipole method (Alg. M)
+def test_multipole_method_energy_and_moves_match_ewald():
+    """Alg. M.3/M.1 with the periodic terms: the energy converges to Ewald
+    geometrically in p and dE of (wrapped) moves matches Ewald differences."""
+    pos, q = uniform_system(32, 4.0, seed=5)
+    a = 4.0
+    Ue = O.ewald_energy(pos, q, a)
+    errs = []
+    for p in (8, 14, 20):
+        s = O.System(pos, q, a, 3, p)
+        s.setup_multipole()
+        errs.append(abs(s.energy() - Ue))
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-6 * abs(Ue)
+    s = O.System(pos, q, a, 3, 20)
+    s.setup_multipole()
+    rng = np.random.default_rng(7)
+    for _ in range(5):
+        j = int(rng.integers(len(q)))
+        rn = (pos[j] + rng.uniform(-0.8, 0.8, 3)) % a
+        dE = s.propose(j, rn)
+        pos2 = pos.copy()
+        pos2[j] = rn
+        dEx = O.ewald_energy(pos2, q, a) - O.ewald_energy(pos, q, a)
+        assert abs(dE - dEx) < 1e-6 * max(1.0, abs(dEx))
+        s.accept(j, rn, dE)
+        pos = pos2
+
+
+def test_multipole_method_free_space_matches_direct_sums():
+    pos, q = uniform_system(48, 8.0, seed=8)
+    s = O.System(pos, q, 8.0, 4, 20, bc=O.BC_FREE)
+    s.setup_multipole()
+    Ud = O.direct_energy(pos, q)
+    assert abs(s.energy() - Ud) < 1e-7 * abs(Ud)
+    rng = np.random.default_rng(9)
+    for _ in range(5):
+        j = int(rng.integers(len(q)))
+        rn = np.clip(pos[j] + rng.uniform(-1.5, 1.5, 3), 0.0, 7.999)
+        dE = s.propose(j, rn)
+        pos2 = pos.copy()
+        pos2[j] = rn
+        dEx = O.direct_energy(pos2, q) - Ud
+        assert abs(dE - dEx) < 1e-7 * max(1.0, abs(dEx))
+        s.accept(j, rn, dE)
+        pos, Ud = pos2, Ud + dEx
+
+
+def test_multipole_method_accepts_equal_fresh_setup_and_track_local_method():
+    """Alg. M.2 adds and removes exactly the terms of Alg. M.3; the
+    multipole and local methods approximate the same dE, so their gap falls
+    with p."""
+    pos, q = uniform_system(128, 8.0, seed=14)
+    a, L = 8.0, 3
+    s = O.System(pos, q, a, L, 8)
+    s.setup_multipole()
+    rng = np.random.default_rng(15)
+    for _ in range(25):
+        j = int(rng.integers(len(q)))
+        rn = (s.positions()[j] + rng.uniform(-1.2, 1.2, 3)) % a
+        s.accept(j, rn, s.propose(j, rn))
+    f = O.System(s.positions(), q, a, L, 8)
+    f.setup_multipole()
+    for lev in range(2, L + 1):
+        A, B = s.multipole(lev), f.multipole(lev)
+        assert np.max(np.abs(A - B)) <= 1e-12 * np.max(np.abs(B))
+    gaps = []
+    for p in (6, 12):
+        m = O.System(pos, q, a, L, p)
+        m.setup_multipole()
+        loc = O.System(pos, q, a, L, p)
+        loc.setup()
+        rng = np.random.default_rng(16)
+        g = 0.0
+        for _ in range(6):
+            j = int(rng.integers(len(q)))
+            rn = (pos[j] + rng.uniform(-0.5, 0.5, 3)) % a
+            g = max(g, abs(m.propose(j, rn) - loc.propose(j, rn)))
+        gaps.append(g)
+    assert gaps[1] < 0.1 * gaps[0] and gaps[1] < 1e-4
