@@ -53,6 +53,10 @@ extern "C" {
                           multipoles, then multipole-to-local over the
                           interaction lists; equal to MC_SETUP_P2L up to the
                           multipole truncation */
+#define MC_SETUP_MULTIPOLE 2 /* the multipole method (Sec. 3.2, alternative
+                          algorithm): Alg. M.3; the context then proposes and
+                          accepts with Alg. M.1/M.2 (a later MC_SETUP_P2L or
+                          MC_SETUP_FMM switches back to the local method) */
 
 typedef struct mc_ctx mc_ctx;
 
@@ -121,6 +125,9 @@ int mc_get_local(mc_ctx *ctx, int level, double *out);
 /* Box multipole K and lattice local expansion H = R(K), real layout, paper
  * normalisation; host arrays of (p+1)^2 doubles (zeros for MC_BC_FREE). */
 int mc_get_far(mc_ctx *ctx, double *K_out, double *H_out);
+/* Multipoles M_n^m of Eq. (4) of every cell of `level` (multipole method
+ * only, else MC_ERR_STATE), layout as mc_get_local. */
+int mc_get_multipole(mc_ctx *ctx, int level, double *out);
 /* Lattice sums S_l^m = sum over integer v with max|v_i| >= 2 of
  * Y_l^m(v/|v|)/|v|^(l+1), l <= lmax <= 30, as computed on the device;
  * complex interleaved, index 2*(l*l + l + m). */

@@ -17,7 +17,7 @@
 #include "mc_dev.cuh"
 
 // kernels defined in the other translation units
-cudaError_t mc_launch_chain(const McSys* d_sys, const RunParams& rp, int prec, int nCTA,
+cudaError_t mc_launch_chain(const McSys* d_sys, const RunParams& rp, int prec, int var, int nCTA,
                             cudaStream_t stream);
 cudaError_t mc_launch_pipe(const McSys* d_sys, const RunParams& rp, int prec, int nCTA,
                            cudaStream_t stream);
@@ -25,7 +25,7 @@ cudaError_t mc_launch_batch_pipe(const McSys* const* d_systems, RunParams* d_rps
                                  const int* d_cta_chain, const int* d_cta_rank,
                                  const int* d_chain_ctas, int prec, int nCTA, cudaStream_t stream);
 cudaError_t mc_launch_batch(const McSys* const* d_systems, RunParams* d_rps, const int* d_cta_chain,
-                            const int* d_cta_rank, const int* d_chain_ctas, int prec, int spec,
+                            const int* d_cta_rank, const int* d_chain_ctas, int prec, int var,
                             int nCTA, cudaStream_t stream);
 int mc_chain_max_ctas(int prec);
 __global__ void k_cell_count(int, const double4*, double, int, int*, int*);
@@ -131,9 +131,10 @@ int launch_chain(mc_ctx* c, RunParams& rp) {
   rp.wait_ns = c->wait_ns;
   rp.bar_missing = c->bar_missing;
   rp.prof = c->d_prof;
-  const bool piped = rp.mode == 0 && c->schedule == MC_SCHEDULE_PIPELINED;
+  const bool mm = c->h.method == 1;
+  const bool piped = !mm && rp.mode == 0 && c->schedule == MC_SCHEDULE_PIPELINED;
   rp.nf_cols = piped ? 4 : MC_NF_COLS;
-  rp.spec = c->schedule == MC_SCHEDULE_PHASED ? 1 : 0;
+  rp.spec = (!mm && c->schedule == MC_SCHEDULE_PHASED) ? 1 : 0;
   rp.chain = 0u;
   CK(cudaMemsetAsync(c->h.bar, 0, sizeof(unsigned long long), c->stream));
   CK(cudaMemsetAsync(c->h.status, 0, sizeof(int), c->stream));
@@ -146,7 +147,8 @@ int launch_chain(mc_ctx* c, RunParams& rp) {
     // the two small-level delta buffers of the speculative accept start clear
     if (rp.spec && c->h.nsmall > 0)
       CK(cudaMemsetAsync(c->h.dsmall, 0, sizeof(double) * 3 * (size_t)c->h.nsmall * c->h.C, c->stream));
-    CK(mc_launch_chain(c->d_sys, rp, c->h.prec, c->nCTA, c->stream));
+    CK(mc_launch_chain(c->d_sys, rp, c->h.prec,
+                       mm ? MC_VAR_MM : (rp.spec ? MC_VAR_SPEC : MC_VAR_PLAIN), c->nCTA, c->stream));
   }
   return MC_OK;
 }
@@ -181,17 +183,14 @@ int run_setup(mc_ctx* c) {
 
 // FMM-variant initialisation (fast mode): multipoles of every level, then
 // multipole-to-local over the interaction lists
-int run_setup_fmm(mc_ctx* c) {
+// per-level multipoles (Eq. 4) of every cell into d_mpole (allocated on
+// first use): the fast setup's first pass and Alg. M.3
+int p2m_levels(mc_ctx* c) {
   McSys& h = c->h;
-  const int C = h.C, p = h.p;
-  const int per = (2 * p + 1) * (2 * p + 2) / 2;
-  if (!c->d_mpole) {
-    if (dalloc(c, (void**)&c->d_mpole, sizeof(double) * (size_t)std::max(1, h.ncell_total) * C) != MC_OK ||
-        dalloc(c, (void**)&c->d_otab, sizeof(double) * 2 * 343 * (size_t)per) != MC_OK)
-      return MC_ERR_NOMEM;
-    k_offset_table<<<grid_for(c->sms, 343 * (size_t)per, 256), 256, 0, c->stream>>>(p, c->d_otab);
-    CK(cudaGetLastError());
-  }
+  const int C = h.C;
+  if (!c->d_mpole &&
+      dalloc(c, (void**)&c->d_mpole, sizeof(double) * (size_t)std::max(1, h.ncell_total) * C) != MC_OK)
+    return MC_ERR_NOMEM;
   for (int l = h.lmin; l <= h.L; l++) {
     const int nl = h.lev_n[l], ncl = nl * nl * nl;
     const int f = 1 << (h.L - l);
@@ -210,6 +209,48 @@ int run_setup_fmm(mc_ctx* c) {
       CK(cudaGetLastError());
     }
   }
+  return MC_OK;
+}
+
+// the box multipole K, dipole and H = G K
+int setup_far(mc_ctx* c) {
+  const int nch = std::min<int>(1024, std::max<int>(1, c->h.n / 64));
+  k_box_multipole<<<grid_for(c->sms, nch, MC_WARPS), MC_THREADS, 0, c->stream>>>(c->d_sys, nch,
+                                                                                c->d_scratch);
+  CK(cudaGetLastError());
+  k_far_finish<<<1, 256, 0, c->stream>>>(c->d_sys, nch, c->d_scratch);
+  CK(cudaGetLastError());
+  return MC_OK;
+}
+
+// the state of one method on the device: method 0 (local) or 1 (multipole)
+int set_method(mc_ctx* c, int method) {
+  c->h.method = method;
+  c->h.Mhat = method ? c->d_mpole : nullptr;
+  CK(cudaMemcpyAsync(c->d_sys, &c->h, sizeof(McSys), cudaMemcpyHostToDevice, c->stream));
+  return MC_OK;
+}
+
+// Alg. M.3 with K/E/H: the multipole method's initialisation
+int run_setup_mm(mc_ctx* c) {
+  int rc = p2m_levels(c);
+  if (rc != MC_OK) return rc;
+  if ((rc = set_method(c, 1)) != MC_OK) return rc;
+  return setup_far(c);
+}
+
+int run_setup_fmm(mc_ctx* c) {
+  McSys& h = c->h;
+  const int C = h.C, p = h.p;
+  const int per = (2 * p + 1) * (2 * p + 2) / 2;
+  if (!c->d_otab) {
+    if (dalloc(c, (void**)&c->d_otab, sizeof(double) * 2 * 343 * (size_t)per) != MC_OK)
+      return MC_ERR_NOMEM;
+    k_offset_table<<<grid_for(c->sms, 343 * (size_t)per, 256), 256, 0, c->stream>>>(p, c->d_otab);
+    CK(cudaGetLastError());
+  }
+  int rc = p2m_levels(c);
+  if (rc != MC_OK) return rc;
   for (int l = h.lmin; l <= h.L; l++) {
     CK(m2l_launch(c->d_sys, p, l, h.lev_n[l], c->sms, c->d_mpole + (size_t)h.lev_off[l] * C,
                   c->d_otab, h.Lhat + (size_t)h.lev_off[l] * C, c->stream));
@@ -475,9 +516,16 @@ int mc_init(mc_ctx** out, int64_t n, const double* pos, const double* q, double 
 }
 
 int mc_setup(mc_ctx* c, int mode) {
-  if (!c || (mode != MC_SETUP_P2L && mode != MC_SETUP_FMM)) return MC_ERR_ARG;
+  if (!c || (mode != MC_SETUP_P2L && mode != MC_SETUP_FMM && mode != MC_SETUP_MULTIPOLE))
+    return MC_ERR_ARG;
   CK(cudaSetDevice(c->dev));
-  int rc = mode == MC_SETUP_FMM ? run_setup_fmm(c) : run_setup(c);
+  int rc;
+  if (mode == MC_SETUP_MULTIPOLE) {
+    rc = run_setup_mm(c);
+  } else {
+    rc = set_method(c, 0);
+    if (rc == MC_OK) rc = mode == MC_SETUP_FMM ? run_setup_fmm(c) : run_setup(c);
+  }
   if (rc != MC_OK) return rc;
   rc = energy_into(c, c->h.energy);
   if (rc != MC_OK) return rc;
@@ -590,7 +638,7 @@ int mc_run(mc_ctx* c, int64_t n_steps, uint64_t seed, double beta, double half_w
     if (resetup_every > 0 && done < n_steps) {
       // full FP64 re-setup from the current positions; drift = running - fresh
       double run_e = 0.0, fresh = 0.0;
-      if ((rc = run_setup(c)) != MC_OK) break;
+      if ((rc = c->h.method ? run_setup_mm(c) : run_setup(c)) != MC_OK) break;
       if ((rc = energy_into(c, c->d_energy_tmp)) != MC_OK) break;
       if (cudaMemcpyAsync(&run_e, c->h.energy, sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
           cudaMemcpyAsync(&fresh, c->d_energy_tmp, sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
@@ -663,6 +711,7 @@ int mc_get_positions(mc_ctx* c, double* pos_out) {
 int mc_get_local(mc_ctx* c, int level, double* out) {
   if (!c || !out) return MC_ERR_ARG;
   if (level < 2 || level > c->h.L) return MC_ERR_LEVELS;
+  if (c->h.method != 0) return MC_ERR_STATE;  // the multipole method keeps no locals
   const int nl = c->h.lev_n[level], C = c->h.C;
   const size_t cnt = (size_t)nl * nl * nl * C;
   if (level < c->h.lmin) {  // free space: the interaction lists of level 2 are empty
@@ -676,6 +725,26 @@ int mc_get_local(mc_ctx* c, int level, double* out) {
   std::vector<double> inv(C);
   for (int k = 0; k < C; k++) inv[k] = 1.0 / scale_of(k);
   for (size_t i = 0; i < cnt; i++) out[i] *= inv[i % C];
+  return MC_OK;
+}
+
+int mc_get_multipole(mc_ctx* c, int level, double* out) {
+  if (!c || !out) return MC_ERR_ARG;
+  if (level < 2 || level > c->h.L) return MC_ERR_LEVELS;
+  if (c->h.method != 1 || !c->d_mpole) return MC_ERR_STATE;
+  const int nl = c->h.lev_n[level], C = c->h.C;
+  const size_t cnt = (size_t)nl * nl * nl * C;
+  if (level < c->h.lmin) {
+    memset(out, 0, sizeof(double) * cnt);
+    return MC_OK;
+  }
+  CK(cudaSetDevice(c->dev));
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(out, c->d_mpole + (size_t)c->h.lev_off[level] * C, sizeof(double) * cnt,
+                cudaMemcpyDeviceToHost));
+  std::vector<double> sc(C);
+  for (int k = 0; k < C; k++) sc[k] = scale_of(k);
+  for (size_t i = 0; i < cnt; i++) out[i] *= sc[i % C];
   return MC_OK;
 }
 
@@ -849,7 +918,7 @@ int batch_set_params(mc_batch* b, long long n_steps, const uint64_t* seeds, doub
     rp.h = h;
     rp.wait_ns = b->ctxs[i]->wait_ns;
     rp.bar_missing = 0u;
-    rp.spec = b->schedule == MC_SCHEDULE_PHASED ? 1 : 0;
+    rp.spec = (b->ctxs[i]->h.method == 0 && b->schedule == MC_SCHEDULE_PHASED) ? 1 : 0;
     rp.nf_cols = b->nf_cols;
     rp.chain = (unsigned)i;
     if (logj) {
@@ -870,12 +939,15 @@ int batch_enqueue(mc_batch* b) {
     CK(cudaMemsetAsync(b->ctxs[i]->h.dsmall, 0,
                        sizeof(double) * 3 * (size_t)b->ctxs[i]->h.nsmall * b->ctxs[i]->h.C, b->stream));
   }
-  if (b->schedule == MC_SCHEDULE_PIPELINED) {
+  if (b->schedule == MC_SCHEDULE_PIPELINED && b->ctxs[0]->h.method == 0) {
     CK(mc_launch_batch_pipe(b->d_systems, b->d_rps, b->d_cta_chain, b->d_cta_rank,
                             b->d_chain_ctas, b->prec, b->nCTA, b->stream));
   } else {
+    const int var = b->ctxs[0]->h.method == 1 ? MC_VAR_MM
+                    : b->schedule == MC_SCHEDULE_PHASED ? MC_VAR_SPEC
+                                                       : MC_VAR_PLAIN;
     CK(mc_launch_batch(b->d_systems, b->d_rps, b->d_cta_chain, b->d_cta_rank, b->d_chain_ctas,
-                       b->prec, b->schedule == MC_SCHEDULE_PHASED ? 1 : 0, b->nCTA, b->stream));
+                       b->prec, var, b->nCTA, b->stream));
   }
   return MC_OK;
 }
@@ -912,7 +984,9 @@ int mc_batch_create(mc_batch** out, int n_chains, mc_ctx* const* ctxs) {
   for (int i = 0; i < n_chains; i++) {
     if (!ctxs[i]) return MC_ERR_ARG;
     if (!ctxs[i]->setup_done) return MC_ERR_STATE;
-    if (ctxs[i]->h.prec != ctxs[0]->h.prec || ctxs[i]->dev != ctxs[0]->dev) return MC_ERR_ARG;
+    if (ctxs[i]->h.prec != ctxs[0]->h.prec || ctxs[i]->dev != ctxs[0]->dev ||
+        ctxs[i]->h.method != ctxs[0]->h.method)
+      return MC_ERR_ARG;
     for (int k = 0; k < i; k++)
       if (ctxs[k] == ctxs[i]) return MC_ERR_ARG;
   }

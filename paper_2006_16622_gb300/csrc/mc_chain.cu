@@ -142,17 +142,22 @@ __device__ __forceinline__ SmallEntry small_entry(const unsigned short (*il)[189
   return se;
 }
 
-// kSpec: speculative accept (MC_SCHEDULE_PHASED) or accept computed after the
-// decision (MC_SCHEDULE_PLAIN), as separate instantiations (smaller code per
-// kernel: the instruction cache is a measured limit of this kernel)
-template <typename TE, bool kSpec>
+// kVar: MC_VAR_PLAIN (local method, accept computed after the decision),
+// MC_VAR_SPEC (local method, speculative accept: MC_SCHEDULE_PHASED) or
+// MC_VAR_MM (the multipole method of Alg. M.1/M.2), as separate
+// instantiations (smaller code per kernel: the instruction cache is a
+// measured limit of this kernel)
+template <typename TE, int kVar>
 __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunParams& rp,
                                            const int nCTA, const int cta) {
+  constexpr bool spec = kVar == MC_VAR_SPEC;
+  constexpr bool mm = kVar == MC_VAR_MM;
   __shared__ McSys S;
   __shared__ HarmTabs<TE> tabs;
   __shared__ unsigned short il[8][189];
-  __shared__ double stage[MC_WARPS][256];
+  __shared__ double stage[MC_WARPS][mm ? 512 : 256];
   __shared__ double s_dE, s_logu, s_u;
+  __shared__ double s_wpart[MC_WARPS];  // per-warp partial sums (multipole method)
   __shared__ StepGeo sgeo;
   // offset of r (side 0) / r' (side 1) from its cell centre on level l
   __shared__ double s_off[2][MC_MAXLEV + 2][3];
@@ -177,7 +182,6 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
   const bool pbc = (S.bc == 0);
   const int nWarpsTot = nCTA * MC_WARPS;
   const int gw = warp * nCTA + cta;  // this warp's first item of every phase
-  constexpr bool spec = kSpec;
   unsigned long long gen = 0;
   long long n_acc = 0, n_border = 0, steps_done = 0;
   const bool prof_on = rp.prof != nullptr;
@@ -379,17 +383,21 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
 
     // ------------------------------------- phase A: propose (+ accept deltas)
     const int nN = same ? 27 : 54;
+    // the multipole method's P items: 95 per level (entries 2k, 2k+1 of
+    // IL(alpha) and IL(alpha') per item, one per 8-lane group)
+    const int nEx = mm ? 95 * nlev : nE;
     // K: the far-field change dK of the next proposal, which depends on
     // positions only, is formed one step ahead; this step's far items use
     // the one formed in the previous step unless that step moved the
     // particle this proposal picks
     const bool k_next = pbc && rp.mode == 0 && t + 1 < rp.nsteps;
     const bool dk_pre = pbc && rp.mode == 0 && t > 0 && !(mv1 && g.j == j1) && !(mv2 && g.j == j2);
-    const int iF = 0, iE = nF, iN = iE + nE, iX = iN + nN, iU = iX + 1, iK = iU + 1;
+    const int iF = 0, iE = nF, iN = iE + nEx, iX = iN + nN, iU = iX + 1, iK = iU + 1;
     const int nProp = k_next ? iK + 1 : iU + 1;
     const int nPhaseA = nProp + ((spec && !idle) ? nDs : 0);
     double* part = S.partials + buf * MC_MAX_ITEMS;
 
+    double wsum = 0.0;  // this warp's items, in item order (multipole method)
     for (int it = gw; it < nPhaseA; it += nWarpsTot) {
       const unsigned long long t_item = prof_on ? mc_globaltimer() : 0ULL;
       int ptype = 7;
@@ -525,6 +533,72 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
         if (it == iX && g.outside) partial = kInf;
         if (it == iU && lane == 0 && rp.mode == 0) part[MC_MAX_ITEMS - 1] = log(u);
         ptype = 3;
+      } else if (mm && it >= iE && it < iN) {
+        // ---- P: Alg. M.1, the multipole expansions (Eq. multipole
+        //      expansion) of entry 2k + grp/2 of IL(alpha) (groups 0, 2) and
+        //      IL(alpha') (groups 1, 3) on level l at r and r'
+        ptype = 0;
+        const int pi = it - iE, lvi = pi / 95, k = pi % 95;
+        const int l = L - lvi, sh = L - l, nl = S.lev_n[l];
+        const int grp = lane >> 3, side = grp & 1;
+        const int co[3] = {g.cf[0] >> sh, g.cf[1] >> sh, g.cf[2] >> sh};
+        const int cn[3] = {g.cfn[0] >> sh, g.cfn[1] >> sh, g.cfn[2] >> sh};
+        const SmallEntry se = small_entry(il, side ? cn : co, nl, pbc, 2 * k + (grp >> 1));
+        TE dx = TE(3), dy = TE(3), dz = TE(3);
+        if (se.valid) {
+          if (sizeof(TE) == 8) {
+            dx = (TE)(s_off[side][l][0] - s_kw[l][se.o[0] + 3]);
+            dy = (TE)(s_off[side][l][1] - s_kw[l][se.o[1] + 3]);
+            dz = (TE)(s_off[side][l][2] - s_kw[l][se.o[2] + 3]);
+          } else {
+            dx = from_double<TE>(s_off[side][l][0]) - s_kwe[l][se.o[0] + 3];
+            dy = from_double<TE>(s_off[side][l][1]) - s_kwe[l][se.o[1] + 3];
+            dz = from_double<TE>(s_off[side][l][2]) - s_kwe[l][se.o[2] + 3];
+          }
+        }
+        const double* Mb =
+            S.Mhat + (size_t)(S.lev_off[l] + (se.t3[0] * nl + se.t3[1]) * nl + se.t3[2]) * C;
+        // the column polynomials of the irregular sets first (positions
+        // only), then the multipoles, which the previous accept may still be
+        // writing
+        TE qsv[MC_PMAX + 2];
+        TE D1r, D1i, D2r, D2i;
+        irregular_group_q<TE>(&tabs, p, dx, dy, dz, &D1r, &D1i, &D2r, &D2i,
+                              [&](int t2, int n, int m, bool v, bool c1, TE qv) {
+                                qsv[t2] = v ? qv : TE(0);
+                              });
+        need_state();
+        double ld[MC_PMAX + 2], lid[MC_PMAX + 2];
+#pragma unroll
+        for (int t2 = 0; t2 <= MC_PMAX + 1; t2++) {
+          int n, m;
+          bool v;
+          group_nm(p, t2, &n, &m, &v);
+          const int kk = rl_re(n, m);
+          ld[t2] = (se.valid && v) ? __ldcg(&Mb[kk]) : 0.0;
+          lid[t2] = (se.valid && v && m) ? __ldcg(&Mb[kk + 1]) : 0.0;
+        }
+        const int m1 = lane & 7, len1 = p - m1 + 1;
+        TE SR = TE(0), SI = TE(0), SR1 = TE(0), SI1 = TE(0);
+#pragma unroll
+        for (int t2 = 0; t2 <= MC_PMAX + 1; t2++) {
+          if (t2 <= p + 1) {
+            const bool sw = t2 == len1;  // first step of column 2
+            SR1 = sw ? SR : SR1;
+            SI1 = sw ? SI : SI1;
+            SR = sw ? TE(0) : SR;
+            SI = sw ? TE(0) : SI;
+            SR += from_double<TE>(ld[t2]) * qsv[t2];
+            SI += from_double<TE>(lid[t2]) * qsv[t2];
+          }
+        }
+        TE acc = (m1 ? TE(2) : TE(1)) * (D1r * SR1 - D1i * SI1) + TE(2) * (D2r * SR - D2i * SI);
+        acc = group_sum(acc);
+        // r' side counts +, r side -; the four groups summed
+        TE sv = se.valid ? (side ? acc : -acc) : TE(0);
+        sv += __shfl_xor_sync(0xffffffffu, sv, 8);
+        sv += __shfl_xor_sync(0xffffffffu, sv, 16);
+        partial = g.q * to_double(sv);
       } else if (it >= iE && it < iN) {
         // ---- E: Eq. (2) at r (group 0) and r' (group 1) on level l
         ptype = 0;
@@ -756,8 +830,24 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
         ptype = 3;
         if (lane == 0 && rp.mode == 0) part[MC_MAX_ITEMS - 1] = log(u);
       }
-      if (lane == 0) part[it] = partial;
+      if (mm) {
+        wsum += partial;
+      } else if (lane == 0) {
+        part[it] = partial;
+      }
       if (prof_on && lane == 0) prof_item(rp.prof, ptype, t_item);
+    }
+    if (mm) {
+      // the multipole method has more items than partial slots: one partial
+      // per CTA, summed over its warps in a fixed order
+      if (lane == 0) s_wpart[warp] = wsum;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double cs = 0.0;
+#pragma unroll
+        for (int w2 = 0; w2 < MC_WARPS; w2++) cs += s_wpart[w2];
+        part[cta] = cs;
+      }
     }
 
     if (prof_lead) {
@@ -779,7 +869,7 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
 #pragma unroll
       for (int i = 0; i < MC_MAX_ITEMS / 32; i++) {
         const int ii = lane + 32 * i;
-        v[i] = ii < nProp ? __ldcg(&part[ii]) : 0.0;
+        v[i] = ii < (mm ? nCTA : nProp) ? __ldcg(&part[ii]) : 0.0;
       }
       const double lu = (rp.mode == 0 && lane == 0) ? __ldcg(&part[MC_MAX_ITEMS - 1]) : 0.0;
       double acc = 0.0;
@@ -839,7 +929,7 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
     // then the Alg. L.2 items (applied from the staged contributions, or
     // computed here when not speculating)
     const int nKH = pbc ? (C + 31) / 32 : 0;
-    const int nB = 1 + nKH + (spec ? S.nsmall + nLB : nD);
+    const int nB = 1 + nKH + (mm ? nlev : (spec ? S.nsmall + nLB : nD));
     for (int it = gw; it < nB; it += nWarpsTot) {
       const unsigned long long t_item = prof_on ? mc_globaltimer() : 0ULL;
       if (it == 0) {
@@ -916,6 +1006,51 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
           __stcg(&S.Hhat[k], hh + gs);
         }
         if (prof_on && lane == 0) prof_item(rp.prof, 6, t_item);
+        continue;
+      }
+      if (mm) {
+        // ---- Alg. M.2 on level l: Mhat(alpha) -= q conj Rt(r - R_alpha)
+        //      (group 0), Mhat(alpha') += q conj Rt(r' - R_alpha') (group 1)
+        const int l = L - (it - 1 - nKH), sh = L - l, nl = S.lev_n[l];
+        const int co[3] = {g.cf[0] >> sh, g.cf[1] >> sh, g.cf[2] >> sh};
+        const int cn[3] = {g.cfn[0] >> sh, g.cfn[1] >> sh, g.cfn[2] >> sh};
+        const int grp = lane >> 3, side = grp & 1;
+        const TE f = grp < 2 ? from_double<TE>(side ? g.q : -g.q) : TE(0);
+        const TE dx = from_double<TE>(s_off[side][l][0]), dy = from_double<TE>(s_off[side][l][1]),
+                 dz = from_double<TE>(s_off[side][l][2]);
+        double* st = stage[warp];
+        regular_group_s<TE>(&tabs, p, dx, dy, dz, f, [&](int t2, int n, int m, bool v, TE vr, TE vi) {
+          if (grp < 2 && v) {
+            const int kk = side * 256 + rl_re(n, m);
+            st[kk] = to_double(vr);
+            if (m) st[kk + 1] = to_double(neg_bits(vi));
+          }
+        });
+        __syncwarp();
+        const bool samel = co[0] == cn[0] && co[1] == cn[1] && co[2] == cn[2];
+        double* M0 = S.Mhat + (size_t)(S.lev_off[l] + (co[0] * nl + co[1]) * nl + co[2]) * C;
+        double* M1 = S.Mhat + (size_t)(S.lev_off[l] + (cn[0] * nl + cn[1]) * nl + cn[2]) * C;
+        double v0[8], v1[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+          const int kk = lane + 32 * i;
+          v0[i] = kk < C ? __ldcg(&M0[kk]) : 0.0;
+          v1[i] = (kk < C && !samel) ? __ldcg(&M1[kk]) : 0.0;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+          const int kk = lane + 32 * i;
+          if (kk < C) {
+            if (samel) {
+              __stcg(&M0[kk], v0[i] + (st[kk] + st[256 + kk]));
+            } else {
+              __stcg(&M0[kk], v0[i] + st[kk]);
+              __stcg(&M1[kk], v1[i] + st[256 + kk]);
+            }
+          }
+        }
+        __syncwarp();
+        if (prof_on && lane == 0) prof_item(rp.prof, 5, t_item);
         continue;
       }
       // ---- Alg. L.2 items
@@ -1087,10 +1222,10 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
 }
 
 // one chain on the whole grid
-template <typename TE, bool kSpec>
+template <typename TE, int kVar>
 __global__ void __launch_bounds__(MC_THREADS, 1)
     mc_chain_kernel(const McSys* __restrict__ sysp, RunParams rp) {
-  chain_body<TE, kSpec>(sysp, rp, (int)gridDim.x, (int)blockIdx.x);
+  chain_body<TE, kVar>(sysp, rp, (int)gridDim.x, (int)blockIdx.x);
 }
 
 // many independent chains: CTA b runs chain cta_chain[b] as rank cta_rank[b]
@@ -1098,7 +1233,7 @@ __global__ void __launch_bounds__(MC_THREADS, 1)
 // barrier counter, partials and status in its McSys); per-chain parameters
 // in device memory, step counter advanced in place so that a replayed graph
 // continues every chain's proposal stream
-template <typename TE, bool kSpec>
+template <typename TE, int kVar>
 __global__ void __launch_bounds__(MC_THREADS, 1)
     mc_batch_kernel(const McSys* const* __restrict__ systems, RunParams* __restrict__ rps,
                     const int* __restrict__ cta_chain, const int* __restrict__ cta_rank,
@@ -1106,7 +1241,7 @@ __global__ void __launch_bounds__(MC_THREADS, 1)
   const int ch = cta_chain[blockIdx.x];
   RunParams rp = rps[ch];
   const McSys* sys = systems[ch];
-  chain_body<TE, kSpec>(sys, rp, chain_ctas[ch], cta_rank[blockIdx.x]);
+  chain_body<TE, kVar>(sys, rp, chain_ctas[ch], cta_rank[blockIdx.x]);
   if (cta_rank[blockIdx.x] == 0 && threadIdx.x == 0) {
     // every CTA of the group read rps[ch] before the group's first barrier
     const long long done = sys->stats[0];
@@ -1114,24 +1249,42 @@ __global__ void __launch_bounds__(MC_THREADS, 1)
   }
 }
 
-template __global__ void mc_chain_kernel<double, true>(const McSys*, RunParams);
-template __global__ void mc_chain_kernel<float, true>(const McSys*, RunParams);
-template __global__ void mc_chain_kernel<double, false>(const McSys*, RunParams);
-template __global__ void mc_chain_kernel<float, false>(const McSys*, RunParams);
+template __global__ void mc_chain_kernel<double, MC_VAR_PLAIN>(const McSys*, RunParams);
+template __global__ void mc_chain_kernel<float, MC_VAR_PLAIN>(const McSys*, RunParams);
+template __global__ void mc_chain_kernel<double, MC_VAR_SPEC>(const McSys*, RunParams);
+template __global__ void mc_chain_kernel<float, MC_VAR_SPEC>(const McSys*, RunParams);
+template __global__ void mc_chain_kernel<double, MC_VAR_MM>(const McSys*, RunParams);
+template __global__ void mc_chain_kernel<float, MC_VAR_MM>(const McSys*, RunParams);
+
+namespace {
+template <int V>
+const void* chain_fn(int prec) {
+  return prec ? (const void*)mc_chain_kernel<float, V> : (const void*)mc_chain_kernel<double, V>;
+}
+template <int V>
+cudaError_t batch_launch(const cudaLaunchConfig_t* cfg, int prec, const McSys* const* d_systems,
+                         RunParams* d_rps, const int* d_cta_chain, const int* d_cta_rank,
+                         const int* d_chain_ctas) {
+  if (prec)
+    return cudaLaunchKernelEx(cfg, mc_batch_kernel<float, V>, d_systems, d_rps, d_cta_chain,
+                              d_cta_rank, d_chain_ctas);
+  return cudaLaunchKernelEx(cfg, mc_batch_kernel<double, V>, d_systems, d_rps, d_cta_chain,
+                            d_cta_rank, d_chain_ctas);
+}
+}  // namespace
 
 // host-side launchers (cooperative launches: all CTAs co-resident)
-cudaError_t mc_launch_chain(const McSys* d_sys, const RunParams& rp, int prec, int nCTA,
+cudaError_t mc_launch_chain(const McSys* d_sys, const RunParams& rp, int prec, int var, int nCTA,
                             cudaStream_t stream) {
   void* args[] = {(void*)&d_sys, (void*)&rp};
-  const void* fn = rp.spec ? (prec ? (const void*)mc_chain_kernel<float, true>
-                                   : (const void*)mc_chain_kernel<double, true>)
-                           : (prec ? (const void*)mc_chain_kernel<float, false>
-                                   : (const void*)mc_chain_kernel<double, false>);
+  const void* fn = var == MC_VAR_MM     ? chain_fn<MC_VAR_MM>(prec)
+                   : var == MC_VAR_SPEC ? chain_fn<MC_VAR_SPEC>(prec)
+                                        : chain_fn<MC_VAR_PLAIN>(prec);
   return cudaLaunchCooperativeKernel(fn, dim3(nCTA), dim3(MC_THREADS), args, 0, stream);
 }
 
 cudaError_t mc_launch_batch(const McSys* const* d_systems, RunParams* d_rps, const int* d_cta_chain,
-                            const int* d_cta_rank, const int* d_chain_ctas, int prec, int spec,
+                            const int* d_cta_rank, const int* d_chain_ctas, int prec, int var,
                             int nCTA, cudaStream_t stream) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nCTA);
@@ -1143,25 +1296,20 @@ cudaError_t mc_launch_batch(const McSys* const* d_systems, RunParams* d_rps, con
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (prec && spec)
-    return cudaLaunchKernelEx(&cfg, mc_batch_kernel<float, true>, d_systems, d_rps, d_cta_chain,
-                              d_cta_rank, d_chain_ctas);
-  if (prec)
-    return cudaLaunchKernelEx(&cfg, mc_batch_kernel<float, false>, d_systems, d_rps, d_cta_chain,
-                              d_cta_rank, d_chain_ctas);
-  if (spec)
-    return cudaLaunchKernelEx(&cfg, mc_batch_kernel<double, true>, d_systems, d_rps, d_cta_chain,
-                              d_cta_rank, d_chain_ctas);
-  return cudaLaunchKernelEx(&cfg, mc_batch_kernel<double, false>, d_systems, d_rps, d_cta_chain,
-                            d_cta_rank, d_chain_ctas);
+  if (var == MC_VAR_MM)
+    return batch_launch<MC_VAR_MM>(&cfg, prec, d_systems, d_rps, d_cta_chain, d_cta_rank, d_chain_ctas);
+  if (var == MC_VAR_SPEC)
+    return batch_launch<MC_VAR_SPEC>(&cfg, prec, d_systems, d_rps, d_cta_chain, d_cta_rank,
+                                     d_chain_ctas);
+  return batch_launch<MC_VAR_PLAIN>(&cfg, prec, d_systems, d_rps, d_cta_chain, d_cta_rank,
+                                    d_chain_ctas);
 }
 
 int mc_chain_max_ctas(int prec) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const void* fn = prec ? (const void*)mc_chain_kernel<float, true>
-                        : (const void*)mc_chain_kernel<double, true>;
+  const void* fn = chain_fn<MC_VAR_SPEC>(prec);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, MC_THREADS, 0);
   if (per < 1) return 0;
   return sms;  // one CTA per SM

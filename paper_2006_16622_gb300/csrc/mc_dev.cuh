@@ -31,6 +31,9 @@
 #define MC_NF_ROWS 6    // far-field row blocks of 32 rows (covers C <= 192)
 #define MC_NF_COLS 16   // far-field column chunks (maximum; RunParams.nf_cols <= this)
 #define MC_GPRE 16      // far-operator columns a warp keeps in registers
+#define MC_VAR_PLAIN 0  // chain kernel variants (see chain_body)
+#define MC_VAR_SPEC 1
+#define MC_VAR_MM 2
 #define MC_DSLOTS 380   // staged accept contributions per level (>= 378 targets)
 
 // ---------------------------------------------------------------- state
@@ -71,6 +74,10 @@ struct McSys {
   // speculative accept: Alg. L.2 contributions staged during the proposal
   double* dacc;      // [2 (step parity) * (L - lmin + 1) * MC_DSLOTS * C]
   double* dKpre;     // [2 * C] dK of the next proposal, by step parity
+  // multipole method (Sec. 3.2, alternative algorithm; method 1): per-level
+  // scaled multipoles Mhat_n^m = sum q conj Rt_n^m(r - R_cell), Lhat's layout
+  int method;
+  double* Mhat;
 };
 
 struct RunParams {
@@ -566,6 +573,17 @@ __device__ __forceinline__ void regular_group_q(const HarmTabs<T>* t, int p, T x
                                                 T* d1i, T* d2r, T* d2i, F&& use) {
   const T r2 = x * x + y * y + z * z;
   harm_group_q<T>(t->rA, t->rB, p, x, y, z, r2, T(1), d1r, d1i, d2r, d2i, use);
+}
+
+// irregular sets in the column-factorised form (unrolled: consumers keep
+// per-step values in register arrays)
+template <typename T, typename F>
+__device__ __forceinline__ void irregular_group_q(const HarmTabs<T>* t, int p, T x, T y, T z, T* d1r,
+                                                  T* d1i, T* d2r, T* d2i, F&& use) {
+  const T r2 = x * x + y * y + z * z;
+  const T ir = mc_rsqrt(r2);
+  const T ir2 = ir * ir;
+  harm_group_q<T>(t->iA, t->iB, p, x * ir2, y * ir2, z * ir2, ir2, ir, d1r, d1i, d2r, d2i, use);
 }
 
 // sign flip on the integer pipe (a negation alone would be an FP64 op)

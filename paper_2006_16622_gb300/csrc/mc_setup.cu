@@ -279,8 +279,10 @@ __global__ void __launch_bounds__(MC_THREADS)
     k_energy_particles(const McSys* __restrict__ sysp, double* __restrict__ out) {
   __shared__ McSys S;
   __shared__ HarmTabs<double> tabs;
+  __shared__ unsigned short il[8][189];
   if (threadIdx.x == 0) S = *sysp;
   harm_tabs_init<double>(&tabs);
+  il_table_init(il);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int p = S.p, C = S.C, L = S.L, nL = S.nL;
@@ -295,7 +297,47 @@ __global__ void __launch_bounds__(MC_THREADS)
     // level expansions: four levels per warp step (one per 8-lane group)
     const int nlev = L - S.lmin + 1;
     const int grp = lane >> 3;
-    for (int l0 = 0; l0 < nlev; l0 += 4) {
+    if (S.method == 1) {
+      // multipole method: the multipole expansions of the cells of the
+      // interaction list on every level, four entries per warp step
+      for (int l = L; l >= S.lmin; l--) {
+        const int sh = L - l, nl = S.lev_n[l];
+        const double w = S.lev_w[l];
+        const int cs[3] = {cf[0] >> sh, cf[1] >> sh, cf[2] >> sh};
+        const int par = ((cs[0] & 1) << 2) | ((cs[1] & 1) << 1) | (cs[2] & 1);
+        for (int e0 = 0; e0 < 189; e0 += 4) {
+          const int e = e0 + grp;
+          int ox = 0, oy = 0, oz = 0;
+          if (e < 189) il_unpack(il[par][e], &ox, &oy, &oz);
+          const int ex[3] = {cs[0] + ox, cs[1] + oy, cs[2] + oz};
+          const bool act = e < 189 && (pbc || (ex[0] >= 0 && ex[0] < nl && ex[1] >= 0 &&
+                                               ex[1] < nl && ex[2] >= 0 && ex[2] < nl));
+          const int t3[3] = {mc_wrap_coord(ex[0], nl), mc_wrap_coord(ex[1], nl),
+                             mc_wrap_coord(ex[2], nl)};
+          const double* Mb = S.Mhat + (size_t)(S.lev_off[l] + (t3[0] * nl + t3[1]) * nl + t3[2]) * C;
+          double Mr[MC_PMAX + 2], Mi[MC_PMAX + 2];
+#pragma unroll
+          for (int t2 = 0; t2 <= MC_PMAX + 1; t2++) {
+            int n, m;
+            bool vld;
+            group_nm(p, t2, &n, &m, &vld);
+            const int k = rl_re(n, m);
+            Mr[t2] = (act && vld) ? Mb[k] : 0.0;
+            Mi[t2] = (act && vld && m) ? Mb[k + 1] : 0.0;
+          }
+          double acc = 0.0;
+          const double dx = act ? v.x - (ex[0] + 0.5) * w : 3.0 * w,
+                       dy = act ? v.y - (ex[1] + 0.5) * w : 3.0 * w,
+                       dz = act ? v.z - (ex[2] + 0.5) * w : 3.0 * w;
+          irregular_group<double>(&tabs, p, dx, dy, dz,
+                                  [&](int t2, int n, int m, bool vld, double cr, double ci) {
+                                    if (vld) acc += (m ? 2.0 : 1.0) * (Mr[t2] * cr - Mi[t2] * ci);
+                                  });
+          if (act) phi += acc;
+        }
+      }
+    }
+    for (int l0 = 0; S.method == 0 && l0 < nlev; l0 += 4) {
       const int li = l0 + grp;
       const bool act = li < nlev;
       const int l = act ? L - li : L;

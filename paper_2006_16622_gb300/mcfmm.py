@@ -19,7 +19,7 @@ BC_PBC, BC_FREE = 0, 1
 TINFOIL, VACUUM = 0, 1
 FP64, FP32_EVAL = 0, 1
 SCHEDULE_PHASED, SCHEDULE_PIPELINED, SCHEDULE_PLAIN = 0, 1, 2
-SETUP_P2L, SETUP_FMM = 0, 1
+SETUP_P2L, SETUP_FMM, SETUP_MULTIPOLE = 0, 1, 2
 PROF_COUNTERS = 56
 
 EXPORTED = ["mc_init", "mc_setup", "mc_propose", "mc_accept", "mc_run", "mc_energy",
@@ -27,7 +27,8 @@ EXPORTED = ["mc_init", "mc_setup", "mc_propose", "mc_accept", "mc_run", "mc_ener
             "mc_lattice_sums", "mc_status", "mc_set_wait_limit", "mc_profile", "mc_profile_read",
             "mc_destroy", "mc_strerror", "mc_p2l_level_noalloc", "mc_batch_create",
             "mc_batch_tune", "mc_batch_run", "mc_batch_info", "mc_batch_destroy",
-            "mc_set_schedule", "mc_batch_set_schedule", "mc_inject_wait_fault"]
+            "mc_set_schedule", "mc_batch_set_schedule", "mc_inject_wait_fault",
+            "mc_get_multipole"]
 
 
 class McStats(ctypes.Structure):
@@ -63,6 +64,7 @@ def load(path: str = LIB_PATH):
     L.mc_energy_fresh.argtypes = [P, P]
     L.mc_get_positions.argtypes = [P, P]
     L.mc_get_local.argtypes = [P, I, P]
+    L.mc_get_multipole.argtypes = [P, I, P]
     L.mc_get_far.argtypes = [P, P, P]
     L.mc_lattice_sums.argtypes = [I, P]
     L.mc_status.argtypes = [P]
@@ -196,6 +198,12 @@ class Context:
         nl = 1 << (level - 1)
         out = np.zeros((nl ** 3, self.C))
         _check(load().mc_get_local(self._h, int(level), _ptr(out)), "mc_get_local")
+        return out
+
+    def multipole(self, level):
+        nl = 1 << (level - 1)
+        out = np.zeros((nl ** 3, self.C))
+        _check(load().mc_get_multipole(self._h, int(level), _ptr(out)), "mc_get_multipole")
         return out
 
     def far(self):
