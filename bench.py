@@ -311,9 +311,10 @@ def huge_workload_leg(args, stream, flush):
 
 def size_sweep_leg(stream):
     """Per-operation times against N (density 0.1, ~20 charges per finest
-    cell, p = 12, h = 0.3): MH steps/s of both forms over 20 000 proposals,
-    and from the device timers of CTA 0 the propose phase (proposal draw to
-    the decision's barrier) and the accept phase per accepted move."""
+    cell, p = 12, h = 0.3): MH steps/s over 20 000 proposals of the local
+    method (FP64 and FP32-eval) and of the multipole method (FP64), and from
+    the device timers of CTA 0 the propose phase (proposal draw to the
+    decision's barrier) and the accept phase per accepted move."""
     import numpy as np
     import torch
 
@@ -324,9 +325,12 @@ def size_sweep_leg(stream):
     for W in size_sweep():
         pos, q = W.system()
         row = {"n": W.n, "levels": W.levels, "p": W.p}
-        for prec, name in ((mcfmm.FP64, "fp64"), (mcfmm.FP32_EVAL, "fp32_eval")):
+        for prec, name, mode in ((mcfmm.FP64, "fp64", None), (mcfmm.FP32_EVAL, "fp32_eval", None),
+                                 (mcfmm.FP64, "multipole_fp64", mcfmm.SETUP_MULTIPOLE)):
             ctx = mcfmm.Context(pos, q, W.a, W.levels, W.p, precision=prec, stream=stream.cuda_stream)
-            ctx.setup(mcfmm.SETUP_FMM if W.n >= 1_000_000 else mcfmm.SETUP_P2L)
+            if mode is None:
+                mode = mcfmm.SETUP_FMM if W.n >= 1_000_000 else mcfmm.SETUP_P2L
+            ctx.setup(mode)
             ctx.run(2000, seed=1, beta=W.beta, half_width=W.half_width, stats=False)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -345,6 +349,8 @@ def size_sweep_leg(stream):
             row[f"{name}_accept_us"] = (pr[3] + pr[4]) / acc / 1e3
             row[f"{name}_acceptance"] = pr[6] / steps
             ctx.close()
+        # time per MH step of the multipole method over the local method
+        row["multipole_over_local_time"] = row["fp64_mh_steps_per_s"] / row["multipole_fp64_mh_steps_per_s"]
         rows.append(row)
     return rows
 
@@ -527,6 +533,10 @@ def gpu_arm(args):
         forms["fp32_eval_plain_schedule"] = world * S * args.steps / r32p["total"]
         forms["fp32_eval_acceptance"] = r32["nu"]
         forms["fp32_eval_setup_s"] = r32["setup_s"]
+    if sweep:
+        row = [r for r in sweep if r["n"] == W.n]
+        if row:
+            forms["multipole_fp64"] = world * row[0]["multipole_fp64_mh_steps_per_s"]
     if rb32:
         forms["batched_fp32_eval"] = world * rb32["value"]
         forms["batched_fp64"] = world * rb64["value"]
