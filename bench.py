@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-huge", action="store_true", help="skip the N=1e6 setup/step leg")
     ap.add_argument("--no-sweep", action="store_true", help="skip the per-operation timing vs N")
+    ap.add_argument("--accuracy", action="store_true",
+                    help="run only the acceptance-probability study (relative error of P vs p)")
+    ap.add_argument("--accuracy-configs", type=int, default=16)
+    ap.add_argument("--accuracy-moves", type=int, default=1000)
     ap.add_argument("--huge-steps", type=int, default=100_000,
                     help="proposals timed per form on the N=1e6 workload")
     return ap.parse_args()
@@ -566,8 +570,62 @@ def gpu_arm(args):
         dist.destroy_process_group()
 
 
+def accuracy_study(args):
+    """Relative error of the acceptance probability, dP = |P - P*| / P*,
+    P = exp(-beta dE), against the number of expansion terms (Sec. 5.1):
+    perturbed 22^3 NaCl crystals at 273 K, `--accuracy-configs` crystals x
+    `--accuracy-moves` proposals (none accepted); P* from the local method at
+    p = 15, the largest order of this build (tests/test_gpu_accuracy.py
+    checks that reference against the p = 25 evaluation the paper uses).
+    Local method in FP64 and FP32-eval, multipole method in FP64, p = 3..14."""
+    import numpy as np
+
+    from paper_2006_16622_gb300 import mcfmm
+    from paper_2006_16622_gb300.workloads import NACL_BETA, perturbed_nacl, study_moves
+
+    mcfmm.load()
+    m, L = 22, 4
+    forms = [("local_fp64", mcfmm.FP64, mcfmm.SETUP_P2L),
+             ("local_fp32_eval", mcfmm.FP32_EVAL, mcfmm.SETUP_P2L),
+             ("multipole_fp64", mcfmm.FP64, mcfmm.SETUP_MULTIPOLE)]
+    ps = list(range(3, 15))
+    errs = {name: {p: [] for p in ps} for name, _, _ in forms}
+    t0 = time.perf_counter()
+    for cfg in range(args.accuracy_configs):
+        pos, q, a = perturbed_nacl(m, seed=cfg)
+        js, rn = study_moves(len(q), a, pos, args.accuracy_moves, seed=cfg)
+
+        def dEs(p, prec, mode):
+            ctx = mcfmm.Context(pos, q, a, L, p, precision=prec)
+            ctx.setup(mode)
+            out = np.array([ctx.propose(int(j), r) for j, r in zip(js, rn)])
+            ctx.close()
+            return out
+
+        ref = np.exp(-NACL_BETA * dEs(15, mcfmm.FP64, mcfmm.SETUP_P2L))
+        for name, prec, mode in forms:
+            for p in ps:
+                P = np.exp(-NACL_BETA * dEs(p, prec, mode))
+                errs[name][p].append(np.abs(P - ref) / np.abs(ref))
+    out = {"metric": "mean relative error of the acceptance probability vs expansion order",
+           "workload": f"perturbed {m}^3 NaCl, spacing 3.3 A, T = 273 K, h = 0.25 A, L = {L}",
+           "samples": args.accuracy_configs * args.accuracy_moves, "reference": "local FP64, p = 15",
+           "mean_delta_p": {}, "p11": {}, "seconds": None}
+    for name, _, _ in forms:
+        out["mean_delta_p"][name] = {p: float(np.mean(np.concatenate(errs[name][p]))) for p in ps}
+        e = np.concatenate(errs[name][11])
+        out["p11"][name] = {"median": float(np.median(e)), "p90": float(np.percentile(e, 90)),
+                            "p99": float(np.percentile(e, 99)), "max": float(e.max()),
+                            "fraction_below_1e-3": float(np.mean(e <= 1e-3))}
+    out["seconds"] = time.perf_counter() - t0
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.accuracy:
+        accuracy_study(args)
+        return
     if args.impl == "reference":
         reference_arm(args)
         return

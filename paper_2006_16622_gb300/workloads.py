@@ -99,3 +99,30 @@ def size_sweep(sizes=(1_000, 10_000, 100_000, 1_000_000), rho: float = 0.1,
         out.append(Workload(f"uniform N={n} rho={rho} a={a:.2f} L={levels} p={p} h={half_width}",
                             n, a, levels, p, 0, half_width))
     return out
+
+
+# The acceptance-probability study (Sec. 5.1): a simple cubic NaCl crystal
+# (lattice constant 3.3 Angstrom, charges +-1 e) with every ion shifted by a
+# uniform random vector of at most 1 % of the lattice constant per axis, at
+# T = 273 K; energies in e^2/Angstrom, so beta = (e^2 / (4 pi eps0 A)) / kT.
+NACL_SPACING = 3.3
+NACL_BETA = 14.399645 / (8.617333262e-5 * 273.0)
+
+
+def perturbed_nacl(m: int, seed: int, spacing: float = NACL_SPACING):
+    """m^3 ions of rock salt, each shifted by U(-0.01, 0.01) x spacing per axis."""
+    pos, q, a = rocksalt(m, spacing)
+    g = _rng(seed)
+    pos = (pos + g.uniform(-0.01 * spacing, 0.01 * spacing, pos.shape)) % a
+    pos = np.minimum(pos, np.nextafter(a, 0.0))
+    return np.ascontiguousarray(pos), q, a
+
+
+def study_moves(n: int, a: float, pos, count: int, seed: int, half_width: float = 0.25):
+    """Seeded proposals (j, r') for the acceptance study: j uniform, r' = r +
+    U(-h, h)^3 wrapped into the box (h = 0.25 Angstrom)."""
+    g = _rng(seed + 7919)
+    js = g.integers(0, n, size=count)
+    rn = (pos[js] + g.uniform(-half_width, half_width, (count, 3))) % a
+    rn = np.minimum(rn, np.nextafter(a, 0.0))
+    return js, rn

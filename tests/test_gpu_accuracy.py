@@ -1,0 +1,52 @@
+"""Acceptance-probability accuracy (Sec. 5.1) on the GPU against the oracle.
+
+dP = |P - P*| / P* with P = exp(-beta dE) at T = 273 K on a perturbed
+12^3 NaCl crystal (spacing 3.3 A), 200 proposals, P* from the oracle's
+local method at p = 25 (the paper's reference).  Checks: the GPU local
+method at p = 15 (the reference of bench.py --accuracy) is two orders below
+the p = 11 error; the error falls with p; at 12 expansion terms (p = 11) the
+mean error is below 1e-3 for both methods (the paper's operating point), with
+the local method the more accurate one at equal p.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2006_16622_gb300 import mcfmm
+from paper_2006_16622_gb300.workloads import NACL_BETA, perturbed_nacl, study_moves
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    mcfmm.load()
+
+
+def test_acceptance_probability_error_against_p25():
+    pos, q, a = perturbed_nacl(12, seed=0)
+    L = 3
+    js, rn = study_moves(len(q), a, pos, 200, seed=0)
+    ref = O.System(pos, q, a, L, 25)
+    ref.setup()
+    p_ref = np.exp(-NACL_BETA * np.array([ref.propose(int(j), r) for j, r in zip(js, rn)]))
+
+    def mean_dp(p, mode):
+        ctx = mcfmm.Context(pos, q, a, L, p)
+        ctx.setup(mode)
+        d = np.array([ctx.propose(int(j), r) for j, r in zip(js, rn)])
+        ctx.close()
+        e = np.abs(np.exp(-NACL_BETA * d) - p_ref) / p_ref
+        return e.mean(), e.max()
+
+    loc = {p: mean_dp(p, mcfmm.SETUP_P2L) for p in (7, 11, 15)}
+    mm11 = mean_dp(11, mcfmm.SETUP_MULTIPOLE)
+    assert loc[7][0] > loc[11][0] > loc[15][0]
+    assert loc[15][0] < 0.2 * loc[11][0] and loc[15][1] < 5e-5
+    assert loc[11][0] < 1e-3 and mm11[0] < 1e-3
+    assert loc[11][0] < mm11[0]
