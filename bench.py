@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-huge", action="store_true", help="skip the N=1e6 setup/step leg")
     ap.add_argument("--no-sweep", action="store_true", help="skip the per-operation timing vs N")
+    ap.add_argument("--no-nacl", action="store_true", help="skip the full-MC NaCl leg")
     ap.add_argument("--accuracy", action="store_true",
                     help="run only the acceptance-probability study (relative error of P vs p)")
     ap.add_argument("--accuracy-configs", type=int, default=16)
@@ -359,6 +360,41 @@ def size_sweep_leg(stream):
     return rows
 
 
+def nacl_full_mc_leg(stream):
+    """The paper's full Monte Carlo setting (Sec. 5.4): 46^3 NaCl ions in a
+    153.2 A box, 12 expansion terms (p = 11), L = 4, T = 273 K, moves of
+    +-0.25 A, with the short-range Lennard-Jones term (12 A cutoff); MH
+    steps/s of both methods (FP64) over 20 000 proposals."""
+    import torch
+
+    from paper_2006_16622_gb300 import mcfmm
+    from paper_2006_16622_gb300.workloads import (NACL_BETA, NACL_FULL_MC, NACL_LJ_CUTOFF,
+                                                  NACL_LJ_EPS, NACL_LJ_SIGMA, nacl_full_mc_system)
+
+    cfg = NACL_FULL_MC
+    pos, q, a = nacl_full_mc_system(cfg["m"], cfg["box"])
+    out = {"workload": f"NaCl {cfg['m']}^3 ions, box {cfg['box']} A, L = {cfg['levels']}, "
+                       f"p = {cfg['p']}, T = 273 K, h = {cfg['half_width']} A, LJ cutoff 12 A"}
+    for name, mode in (("local_fp64", mcfmm.SETUP_P2L), ("multipole_fp64", mcfmm.SETUP_MULTIPOLE)):
+        ctx = mcfmm.Context(pos, q, a, cfg["levels"], cfg["p"], stream=stream.cuda_stream)
+        ctx.set_lj(NACL_LJ_EPS, NACL_LJ_SIGMA, NACL_LJ_CUTOFF)
+        ctx.setup(mode)
+        ctx.run(2000, seed=1, beta=NACL_BETA, half_width=cfg["half_width"], stats=False)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.run(20_000, seed=2, beta=NACL_BETA, half_width=cfg["half_width"], stats=False)
+        e1.record(stream)
+        e1.synchronize()
+        out[f"{name}_mh_steps_per_s"] = 20_000 / (e0.elapsed_time(e1) / 1000.0)
+        st = ctx.run(5000, seed=3, beta=NACL_BETA, half_width=cfg["half_width"])
+        out[f"{name}_acceptance"] = st["accepted"] / max(1, st["steps"])
+        if ctx.status() != 0:
+            raise RuntimeError("NaCl chain failed")
+        ctx.close()
+    return out
+
+
 def precision_form_stats(W, stream):
     """FP32-eval vs the (oracle-parity-tested) FP64 chain on the same seed:
     per-proposal dE error over the common prefix of the two chains, and the
@@ -481,6 +517,7 @@ def gpu_arm(args):
     prec_stats = None if args.no_precision else precision_form_stats(W, stream)
     huge = None if (args.no_huge or rank != 0) else huge_workload_leg(args, stream, flush)
     sweep = None if (args.no_sweep or rank != 0) else size_sweep_leg(stream)
+    nacl = None if (args.no_nacl or rank != 0) else nacl_full_mc_leg(stream)
 
     # end to end through the C ABI: host arrays in, positions and energy out
     e2e = None
@@ -564,7 +601,7 @@ def gpu_arm(args):
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": args.steps, "clocks": r64["clocks"], "forms": forms,
             "precision_form": prec_stats,
-            "setup_s": r64["setup_s"], "huge": huge, "size_sweep": sweep}
+            "setup_s": r64["setup_s"], "huge": huge, "size_sweep": sweep, "nacl_full_mc": nacl}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -125,6 +125,15 @@ int mc_get_local(mc_ctx *ctx, int level, double *out);
 /* Box multipole K and lattice local expansion H = R(K), real layout, paper
  * normalisation; host arrays of (p+1)^2 doubles (zeros for MC_BC_FREE). */
 int mc_get_far(mc_ctx *ctx, double *K_out, double *H_out);
+/* Short-range Lennard-Jones pair term 4 eps((sigma/r)^12 - (sigma/r)^6) for
+ * r < cutoff between different particles (Sec. 5.4: the paper adds a
+ * repulsive Lennard-Jones potential with a 12 Angstrom cutoff to its full
+ * MC runs and gives no parameters); eps = 0 switches it off.  The cutoff may
+ * not exceed the finest cell width (every pair in range is then a near-cell
+ * pair of Alg. 1), else MC_ERR_ARG.  Call mc_setup again afterwards
+ * (MC_ERR_STATE until then).  Not applied by MC_SCHEDULE_PIPELINED, which
+ * falls back to the phased schedule while it is on. */
+int mc_set_lj(mc_ctx *ctx, double eps, double sigma, double cutoff);
 /* Multipoles M_n^m of Eq. (4) of every cell of `level` (multipole method
  * only, else MC_ERR_STATE), layout as mc_get_local. */
 int mc_get_multipole(mc_ctx *ctx, int level, double *out);

@@ -64,6 +64,7 @@ def lib():
             L.orc_setup_fmm.argtypes = [_P]
             L.orc_fmm_local_cell.argtypes = [_P, ctypes.c_int, _P, _P]
             L.orc_setup_multipole.argtypes = [_P]
+            L.orc_set_lj.argtypes = [_P, _D, _D, _D]
             L.orc_get_multipole.argtypes = [_P, ctypes.c_int, _P]
             L.orc_propose.restype = _D
             L.orc_propose.argtypes = [_P, _I64, _P]
@@ -218,6 +219,10 @@ class System:
 
     def setup_fmm(self):
         lib().orc_setup_fmm(self._h)
+
+    def set_lj(self, eps, sig, rc):
+        if lib().orc_set_lj(self._h, float(eps), float(sig), float(rc)) != 0:
+            raise ValueError("bad Lennard-Jones parameters (rc must not exceed the finest cell width)")
 
     def setup_multipole(self):
         lib().orc_setup_multipole(self._h)

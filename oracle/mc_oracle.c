@@ -372,6 +372,9 @@ struct orc_sys {
    * coefficients M_{l,alpha} of Eq. (4), same indexing; method 1 selects it */
   int method;
   cplx *Mx[16];
+  /* short-range Lennard-Jones pair term (Sec. 5.4): 4 eps ((sig/r)^12 -
+   * (sig/r)^6) for r < rc, off when eps = 0 */
+  double lj_eps, lj_sig, lj_rc;
   /* periodic far field: box multipole K, its conjugate E, lattice sums */
   cplx *K, *E, *Slat;
   double D[3];
@@ -727,6 +730,16 @@ void orc_setup_multipole(orc_sys *s) {
   s->energy = orc_energy_fresh(s);
 }
 
+/* switch on the Lennard-Jones term; rc must not exceed the finest cell
+ * width (every pair within rc is in the 27 near cells); -1 otherwise */
+int orc_set_lj(orc_sys *s, double eps, double sig, double rc) {
+  if (eps < 0.0 || sig <= 0.0 || rc <= 0.0 || rc > cell_width(s, s->L)) return -1;
+  s->lj_eps = eps;
+  s->lj_sig = sig;
+  s->lj_rc = rc;
+  return 0;
+}
+
 /* multipoles of level `level` (real layout of the unscaled M_n^m) */
 int orc_get_multipole(const orc_sys *s, int level, double *out) {
   if (level < 2 || level > s->L || !s->Mx[level]) return -1;
@@ -830,6 +843,37 @@ static double dipole_energy(const orc_sys *s, const double D[3]) {
   return -2.0 * M_PI / (3.0 * V) * (D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
 }
 
+/* Lennard-Jones pair energy, truncated at rc (0 beyond) */
+static double lj_pair(const orc_sys *s, double r) {
+  if (s->lj_eps == 0.0 || r >= s->lj_rc) return 0.0;
+  double sr6 = pow(s->lj_sig / r, 6.0);
+  return 4.0 * s->lj_eps * (sr6 * sr6 - sr6);
+}
+
+/* Lennard-Jones energy of particle at x (id i, excluded with all its
+ * images: they lie beyond rc) with the charges of the 27 near cells */
+static double lj_particle(orc_sys *s, int64_t i, const double x[3]) {
+  if (s->lj_eps == 0.0) return 0.0;
+  int cf[3];
+  finest_cell(s, x, cf);
+  double u = 0.0;
+  for (int dx = -1; dx <= 1; dx++)
+    for (int dy = -1; dy <= 1; dy++)
+      for (int dz = -1; dz <= 1; dz++) {
+        int e[3] = {cf[0] + dx, cf[1] + dy, cf[2] + dz}, cc[3], sh[3];
+        if (!wrap_cell(s, s->nL, e, cc, sh)) continue;
+        int cell = lin(s->nL, cc);
+        for (int k = 0; k < s->cnt[cell]; k++) {
+          int64_t t = s->items[cell][k];
+          if (t == i) continue;
+          double d[3];
+          for (int w = 0; w < 3; w++) d[w] = x[w] - (s->pos[3 * t + w] + sh[w] * s->a);
+          u += lj_pair(s, sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
+        }
+      }
+  return u;
+}
+
 /* potential at particle i from everything except itself at its own
  * position: level expansions plus direct near cells */
 static double phi_particle(orc_sys *s, int64_t i) {
@@ -860,7 +904,8 @@ static double phi_particle(orc_sys *s, int64_t i) {
 
 double orc_energy_fresh(orc_sys *s) {
   double U = 0.0;
-  for (int64_t i = 0; i < s->n; i++) U += 0.5 * s->q[i] * phi_particle(s, i);
+  for (int64_t i = 0; i < s->n; i++)
+    U += 0.5 * s->q[i] * phi_particle(s, i) + 0.5 * lj_particle(s, i, &s->pos[3 * i]);
   if (s->bc == ORC_BC_PBC) {
     U += far_energy(s, s->K, s->E);
     U += dipole_energy(s, s->D);
@@ -945,6 +990,10 @@ double orc_propose(orc_sys *s, int64_t j, const double rnew[3]) {
     double d[3] = {rnew[0] - r[0], rnew[1] - r[1], rnew[2] - r[2]};
     dU_dir -= q * q / sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
   }
+
+  /* short-range Lennard-Jones change (the moving particle's own copy and
+   * images excluded on both sides) */
+  dU_dir += lj_particle(s, j, rnew) - lj_particle(s, j, r);
 
   double dU_far = 0.0, dU_dip = 0.0;
   if (s->bc == ORC_BC_PBC) {

@@ -62,6 +62,9 @@ int orc_fmm_local_cell(orc_sys *s, int level, const int c[3], double *out);
  * U0; afterwards propose/accept/run/energy follow Alg. M.1/M.2.  orc_setup
  * or orc_setup_fmm switch back to the local method. */
 void orc_setup_multipole(orc_sys *s);
+/* short-range Lennard-Jones term 4 eps((sig/r)^12 - (sig/r)^6), r < rc
+ * (Sec. 5.4; call before a setup); rc <= finest cell width, else -1 */
+int orc_set_lj(orc_sys *s, double eps, double sig, double rc);
 /* level multipoles M_n^m (real layout), -1 for a bad level or before setup */
 int orc_get_multipole(const orc_sys *s, int level, double *out);
 double orc_propose(orc_sys *s, int64_t j, const double rnew[3]);  /* Alg. L.1 */

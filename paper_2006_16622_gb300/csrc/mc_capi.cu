@@ -132,7 +132,8 @@ int launch_chain(mc_ctx* c, RunParams& rp) {
   rp.bar_missing = c->bar_missing;
   rp.prof = c->d_prof;
   const bool mm = c->h.method == 1;
-  const bool piped = !mm && rp.mode == 0 && c->schedule == MC_SCHEDULE_PIPELINED;
+  // the pipelined kernel has no Lennard-Jones term: phased instead
+  const bool piped = !mm && !c->h.lj_on && rp.mode == 0 && c->schedule == MC_SCHEDULE_PIPELINED;
   rp.nf_cols = piped ? 4 : MC_NF_COLS;
   rp.spec = (!mm && c->schedule == MC_SCHEDULE_PHASED) ? 1 : 0;
   rp.chain = 0u;
@@ -728,6 +729,22 @@ int mc_get_local(mc_ctx* c, int level, double* out) {
   return MC_OK;
 }
 
+int mc_set_lj(mc_ctx* c, double eps, double sigma, double cutoff) {
+  if (!c || !(eps >= 0.0) || !(sigma > 0.0) || !(cutoff > 0.0)) return MC_ERR_ARG;
+  if (cutoff > c->h.lev_w[c->h.L]) return MC_ERR_ARG;  // pairs in range must be near-cell pairs
+  CK(cudaSetDevice(c->dev));
+  const double s6 = pow(sigma, 6.0);
+  c->h.lj_on = eps > 0.0 ? 1 : 0;
+  c->h.lj_eps4 = 4.0 * eps;
+  c->h.lj_s6 = s6;
+  c->h.lj_s12 = s6 * s6;
+  c->h.lj_rc2 = cutoff * cutoff;
+  CK(cudaMemcpyAsync(c->d_sys, &c->h, sizeof(McSys), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->setup_done = 0;  // the energy changes: set up again
+  return MC_OK;
+}
+
 int mc_get_multipole(mc_ctx* c, int level, double* out) {
   if (!c || !out) return MC_ERR_ARG;
   if (level < 2 || level > c->h.L) return MC_ERR_LEVELS;
@@ -939,7 +956,9 @@ int batch_enqueue(mc_batch* b) {
     CK(cudaMemsetAsync(b->ctxs[i]->h.dsmall, 0,
                        sizeof(double) * 3 * (size_t)b->ctxs[i]->h.nsmall * b->ctxs[i]->h.C, b->stream));
   }
-  if (b->schedule == MC_SCHEDULE_PIPELINED && b->ctxs[0]->h.method == 0) {
+  bool any_lj = false;
+  for (int i = 0; i < b->n; i++) any_lj = any_lj || b->ctxs[i]->h.lj_on;
+  if (b->schedule == MC_SCHEDULE_PIPELINED && b->ctxs[0]->h.method == 0 && !any_lj) {
     CK(mc_launch_batch_pipe(b->d_systems, b->d_rps, b->d_cta_chain, b->d_cta_rank,
                             b->d_chain_ctas, b->prec, b->nCTA, b->stream));
   } else {

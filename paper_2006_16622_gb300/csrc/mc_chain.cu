@@ -737,20 +737,30 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
             const double ox = g.r[0] - sx, oy = g.r[1] - sy, oz = g.r[2] - sz;
             const double nx = g.rn[0] - sx, ny = g.rn[1] - sy, nz = g.rn[2] - sz;
             double acc = 0.0;
+            const bool lj = S.lj_on != 0;
             for (int s = lane; s < cnt; s += 32) {
               const double4 xi = ldcg4(&S.cpos[(size_t)cell * S.cap + s]);
+              const int pid = (side != 1 || lj) ? __ldcg(&S.cpid[(size_t)cell * S.cap + s]) : -1;
               if (side != 1) {
-                const int pid = __ldcg(&S.cpid[(size_t)cell * S.cap + s]);
                 if (!(pid == g.j && zero_shift)) {
                   const double ax = ox - xi.x, ay = oy - xi.y, az = oz - xi.z;
-                  acc -= g.q * xi.w * rsqrt(ax * ax + ay * ay + az * az);
+                  const double d2 = ax * ax + ay * ay + az * az;
+                  const double ir = rsqrt(d2);
+                  acc -= g.q * xi.w * ir;
+                  if (lj && pid != g.j)
+                    acc -= lj_energy(ir * ir, d2, S.lj_eps4, S.lj_s6, S.lj_s12, S.lj_rc2);
                 }
               }
               if (side != 0) {
                 const double bx = nx - xi.x, by = ny - xi.y, bz = nz - xi.z;
                 const double d2 = bx * bx + by * by + bz * bz;
                 if (d2 == 0.0) ovl = true;
-                acc += g.q * xi.w * rsqrt(d2);
+                const double ir = rsqrt(d2);
+                acc += g.q * xi.w * ir;
+                // the moving particle's old copy (and its images, beyond the
+                // cutoff) has no Lennard-Jones term
+                if (lj && pid != g.j)
+                  acc += lj_energy(ir * ir, d2, S.lj_eps4, S.lj_s6, S.lj_s12, S.lj_rc2);
               }
             }
             partial = warp_sum(acc);
@@ -769,20 +779,28 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
                         nz = d2f_int(s_off[1][L][2] - on2 * wL);
             float acc = 0.0f;
             const float qf = d2f_int(g.q);
+            const bool lj = S.lj_on != 0;
+            const float e4 = d2f_int(S.lj_eps4), s6 = d2f_int(S.lj_s6), s12 = d2f_int(S.lj_s12),
+                        rc2 = d2f_int(S.lj_rc2);
             for (int s = lane; s < cnt; s += 32) {
               const float4 xi = __ldcg(&S.cpos32[(size_t)cell * S.cap + s]);
+              const int pid = (side != 1 || lj) ? __ldcg(&S.cpid[(size_t)cell * S.cap + s]) : -1;
               if (side != 1) {
-                const int pid = __ldcg(&S.cpid[(size_t)cell * S.cap + s]);
                 if (!(pid == g.j && zero_shift)) {
                   const float ax = ox - xi.x, ay = oy - xi.y, az = oz - xi.z;
-                  acc -= qf * xi.w * rsqrtf(ax * ax + ay * ay + az * az);
+                  const float d2 = ax * ax + ay * ay + az * az;
+                  const float ir = rsqrtf(d2);
+                  acc -= qf * xi.w * ir;
+                  if (lj && pid != g.j) acc -= lj_energy(ir * ir, d2, e4, s6, s12, rc2);
                 }
               }
               if (side != 0) {
                 const float bx = nx - xi.x, by = ny - xi.y, bz = nz - xi.z;
                 const float d2 = bx * bx + by * by + bz * bz;
                 if (d2 == 0.0f) ovl = true;
-                acc += qf * xi.w * rsqrtf(d2);
+                const float ir = rsqrtf(d2);
+                acc += qf * xi.w * ir;
+                if (lj && pid != g.j) acc += lj_energy(ir * ir, d2, e4, s6, s12, rc2);
               }
             }
             partial = f2d_int(warp_sum(acc));

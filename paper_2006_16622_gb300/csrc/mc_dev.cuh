@@ -78,6 +78,10 @@ struct McSys {
   // scaled multipoles Mhat_n^m = sum q conj Rt_n^m(r - R_cell), Lhat's layout
   int method;
   double* Mhat;
+  // short-range Lennard-Jones term (Sec. 5.4): 4 eps ((sig/r)^12 - (sig/r)^6)
+  // for r^2 < rc2, between different particles of the near cells
+  int lj_on;
+  double lj_eps4, lj_s6, lj_s12, lj_rc2;
 };
 
 struct RunParams {
@@ -584,6 +588,13 @@ __device__ __forceinline__ void irregular_group_q(const HarmTabs<T>* t, int p, T
   const T ir = mc_rsqrt(r2);
   const T ir2 = ir * ir;
   harm_group_q<T>(t->iA, t->iB, p, x * ir2, y * ir2, z * ir2, ir2, ir, d1r, d1i, d2r, d2i, use);
+}
+
+// Lennard-Jones pair energy from 1/r^2 (0 at or beyond the cutoff)
+template <typename T>
+__device__ __forceinline__ T lj_energy(T inv2, T d2, T eps4, T s6, T s12, T rc2) {
+  const T inv6 = inv2 * inv2 * inv2;
+  return d2 < rc2 ? eps4 * (s12 * inv6 * inv6 - s6 * inv6) : T(0);
 }
 
 // sign flip on the integer pipe (a negation alone would be an FP64 op)

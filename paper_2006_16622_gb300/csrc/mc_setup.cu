@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(MC_THREADS)
     const double4 v = S.ppos[i];
     const int cf[3] = {finest_coord(v.x, S.inv_wL, nL), finest_coord(v.y, S.inv_wL, nL),
                        finest_coord(v.z, S.inv_wL, nL)};
-    double phi = 0.0;
+    double phi = 0.0, ulj = 0.0;
     // level expansions: four levels per warp step (one per 8-lane group)
     const int nlev = L - S.lmin + 1;
     const int grp = lane >> 3;
@@ -385,11 +385,16 @@ __global__ void __launch_bounds__(MC_THREADS)
         if (pid == i && zs) continue;
         const double4 xi = S.cpos[(size_t)cell * S.cap + s];
         const double ax = v.x - (xi.x + sx), ay = v.y - (xi.y + sy), az = v.z - (xi.z + sz);
-        phi += xi.w * rsqrt(ax * ax + ay * ay + az * az);
+        const double d2 = ax * ax + ay * ay + az * az;
+        const double ir = rsqrt(d2);
+        phi += xi.w * ir;
+        if (S.lj_on && pid != i)  // (i's images lie beyond the cutoff)
+          ulj += lj_energy(ir * ir, d2, S.lj_eps4, S.lj_s6, S.lj_s12, S.lj_rc2);
       }
     }
     phi = warp_sum(phi);
-    usum += 0.5 * v.w * phi;
+    ulj = warp_sum(ulj);
+    usum += 0.5 * (v.w * phi + ulj);
   }
   if (lane == 0) out[gw] = usum;
 }

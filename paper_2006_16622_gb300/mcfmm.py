@@ -28,7 +28,7 @@ EXPORTED = ["mc_init", "mc_setup", "mc_propose", "mc_accept", "mc_run", "mc_ener
             "mc_destroy", "mc_strerror", "mc_p2l_level_noalloc", "mc_batch_create",
             "mc_batch_tune", "mc_batch_run", "mc_batch_info", "mc_batch_destroy",
             "mc_set_schedule", "mc_batch_set_schedule", "mc_inject_wait_fault",
-            "mc_get_multipole"]
+            "mc_get_multipole", "mc_set_lj"]
 
 
 class McStats(ctypes.Structure):
@@ -65,6 +65,7 @@ def load(path: str = LIB_PATH):
     L.mc_get_positions.argtypes = [P, P]
     L.mc_get_local.argtypes = [P, I, P]
     L.mc_get_multipole.argtypes = [P, I, P]
+    L.mc_set_lj.argtypes = [P, D, D, D]
     L.mc_get_far.argtypes = [P, P, P]
     L.mc_lattice_sums.argtypes = [I, P]
     L.mc_status.argtypes = [P]
@@ -199,6 +200,9 @@ class Context:
         out = np.zeros((nl ** 3, self.C))
         _check(load().mc_get_local(self._h, int(level), _ptr(out)), "mc_get_local")
         return out
+
+    def set_lj(self, eps, sigma, cutoff):
+        _check(load().mc_set_lj(self._h, float(eps), float(sigma), float(cutoff)), "mc_set_lj")
 
     def multipole(self, level):
         nl = 1 << (level - 1)

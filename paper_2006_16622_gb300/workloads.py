@@ -126,3 +126,20 @@ def study_moves(n: int, a: float, pos, count: int, seed: int, half_width: float 
     rn = (pos[js] + g.uniform(-half_width, half_width, (count, 3))) % a
     rn = np.minimum(rn, np.nextafter(a, 0.0))
     return js, rn
+
+
+# Full Monte Carlo NaCl runs (Sec. 5.4): the paper adds a repulsive
+# Lennard-Jones term with a 12 Angstrom cutoff and gives no parameters;
+# reading: epsilon = 0.1 eV (in e^2/Angstrom) and sigma with the well
+# minimum at the lattice spacing.  Largest crystal: 46^3 ions in a 153.2
+# Angstrom box, 12 expansion terms (p = 11), moves of +-0.25 Angstrom.
+NACL_LJ_EPS = 0.1 / 14.399645
+NACL_LJ_SIGMA = NACL_SPACING / 2.0 ** (1.0 / 6.0)
+NACL_LJ_CUTOFF = 12.0
+NACL_FULL_MC = dict(m=46, box=153.2, levels=4, p=11, half_width=0.25)
+
+
+def nacl_full_mc_system(m: int = 46, box: float = 153.2, seed: int = 0):
+    """m^3 rock salt in a cube of side `box` (spacing box/m), perturbed by
+    1 % of the spacing (the starting state of the paper's full MC runs)."""
+    return perturbed_nacl(m, seed=seed, spacing=box / m)

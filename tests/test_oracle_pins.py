@@ -493,3 +493,42 @@ def test_multipole_method_accepts_equal_fresh_setup_and_track_local_method():
             g = max(g, abs(m.propose(j, rn) - loc.propose(j, rn)))
         gaps.append(g)
     assert gaps[1] < 0.1 * gaps[0] and gaps[1] < 1e-4
+
+
+# ------------------------------------------- short-range Lennard-Jones term
+def _lj_brute(pos, a, eps, sig, rc, skip=None):
+    """all pairs, minimum image (a >= 2 rc, so at most one image is in range)"""
+    u = 0.0
+    n = len(pos)
+    for i in range(n):
+        for k in range(i + 1, n):
+            d = pos[i] - pos[k]
+            d -= a * np.round(d / a)
+            r = np.linalg.norm(d)
+            if r < rc:
+                u += 4 * eps * ((sig / r) ** 12 - (sig / r) ** 6)
+    return u
+
+
+def test_lennard_jones_energy_and_moves_match_pair_sums():
+    """The LJ term of Sec. 5.4 (cutoff no larger than the finest cell, so
+    the 27 near cells hold every pair in range): energy and dE equal direct
+    minimum-image pair sums; the moving particle's old copy is excluded."""
+    a, L, rc, eps, sig = 24.0, 2, 12.0, 0.02, 1.1
+    pos, q = uniform_system(60, a, seed=41)
+    base = O.System(pos, q, a, L, 8)
+    base.setup()
+    s = O.System(pos, q, a, L, 8)
+    s.set_lj(eps, sig, rc)
+    s.setup()
+    assert abs((s.energy() - base.energy()) - _lj_brute(pos, a, eps, sig, rc)) < 1e-10
+    rng = np.random.default_rng(42)
+    for _ in range(4):
+        j = int(rng.integers(len(q)))
+        rn = (pos[j] + rng.uniform(-0.4, 0.4, 3)) % a
+        pos2 = pos.copy()
+        pos2[j] = rn
+        dlj = _lj_brute(pos2, a, eps, sig, rc) - _lj_brute(pos, a, eps, sig, rc)
+        assert abs((s.propose(j, rn) - base.propose(j, rn)) - dlj) < 1e-10
+    with pytest.raises(ValueError):
+        s.set_lj(eps, sig, 12.5)  # beyond the finest cell width
