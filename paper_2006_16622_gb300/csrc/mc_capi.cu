@@ -28,6 +28,8 @@ cudaError_t mc_launch_batch(const McSys* const* d_systems, RunParams* d_rps, con
                             const int* d_cta_rank, const int* d_chain_ctas, int prec, int var,
                             int nCTA, cudaStream_t stream);
 int mc_chain_max_ctas(int prec);
+int mc_batch_max_ctas(int prec);
+int mc_batch_pipe_ctas_per_sm(int prec);
 __global__ void k_cell_count(int, const double4*, double, int, int*, int*);
 __global__ void k_cell_fill(int, const int*, int, int*, int*);
 __global__ void k_cell_sort(int, int, int, double, const int*, const double4*, int*, double4*,
@@ -1019,7 +1021,16 @@ int mc_batch_create(mc_batch** out, int n_chains, mc_ctx* const* ctxs) {
     delete b;
     return MC_ERR_CUDA;
   }
-  b->sms = ctxs[0]->nCTA;
+  {
+    // the batch's CTAs: its kernels' occupancy (pipelined kernel included)
+    int dev_sms = 0;
+    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, b->dev);
+    b->sms = std::min(mc_batch_max_ctas(b->prec), dev_sms * mc_batch_pipe_ctas_per_sm(b->prec));
+  }
+  if (b->sms < 1) {
+    delete b;
+    return MC_ERR_CUDA;
+  }
   if (n_chains > b->sms) {
     delete b;
     return MC_ERR_ARG;  // every chain needs at least one CTA

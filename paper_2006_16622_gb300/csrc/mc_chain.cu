@@ -28,6 +28,8 @@
 // lattice operator, decision).
 #include "mc_dev.cuh"
 
+#include <algorithm>
+
 namespace {
 
 constexpr double kImageConst = 6.0 + 8.0 / 1.7320508075688772 + 12.0 / 1.4142135623730951;
@@ -1252,7 +1254,7 @@ __global__ void __launch_bounds__(MC_THREADS, 1)
 // in device memory, step counter advanced in place so that a replayed graph
 // continues every chain's proposal stream
 template <typename TE, int kVar>
-__global__ void __launch_bounds__(MC_THREADS, 1)
+__global__ void __launch_bounds__(MC_THREADS, MC_BATCH_CTAS_PER_SM)
     mc_batch_kernel(const McSys* const* __restrict__ systems, RunParams* __restrict__ rps,
                     const int* __restrict__ cta_chain, const int* __restrict__ cta_rank,
                     const int* __restrict__ chain_ctas) {
@@ -1321,6 +1323,25 @@ cudaError_t mc_launch_batch(const McSys* const* d_systems, RunParams* d_rps, con
                                      d_chain_ctas);
   return batch_launch<MC_VAR_PLAIN>(&cfg, prec, d_systems, d_rps, d_cta_chain, d_cta_rank,
                                     d_chain_ctas);
+}
+
+// CTAs the batched form can keep co-resident (its kernels' occupancy x SMs)
+int mc_batch_max_ctas(int prec) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const void* fns[3][2] = {
+      {(const void*)mc_batch_kernel<double, MC_VAR_PLAIN>, (const void*)mc_batch_kernel<float, MC_VAR_PLAIN>},
+      {(const void*)mc_batch_kernel<double, MC_VAR_SPEC>, (const void*)mc_batch_kernel<float, MC_VAR_SPEC>},
+      {(const void*)mc_batch_kernel<double, MC_VAR_MM>, (const void*)mc_batch_kernel<float, MC_VAR_MM>}};
+  int best = 1 << 30;
+  for (int v = 0; v < 3; v++) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fns[v][prec ? 1 : 0], MC_THREADS, 0) !=
+        cudaSuccess)
+      return 0;
+    best = std::min(best, per);
+  }
+  return best < 1 ? 0 : sms * std::min(best, MC_BATCH_CTAS_PER_SM);
 }
 
 int mc_chain_max_ctas(int prec) {

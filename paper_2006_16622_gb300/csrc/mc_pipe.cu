@@ -911,7 +911,7 @@ __global__ void __launch_bounds__(MC_THREADS, 1)
 }
 
 template <typename TE>
-__global__ void __launch_bounds__(MC_THREADS, 1)
+__global__ void __launch_bounds__(MC_THREADS, MC_BATCH_CTAS_PER_SM)
     mc_batch_pipe_kernel(const McSys* const* __restrict__ systems, RunParams* __restrict__ rps,
                          const int* __restrict__ cta_chain, const int* __restrict__ cta_rank,
                          const int* __restrict__ chain_ctas) {
@@ -949,4 +949,12 @@ cudaError_t mc_launch_batch_pipe(const McSys* const* d_systems, RunParams* d_rps
                               d_cta_rank, d_chain_ctas);
   return cudaLaunchKernelEx(&cfg, mc_batch_pipe_kernel<double>, d_systems, d_rps, d_cta_chain,
                             d_cta_rank, d_chain_ctas);
+}
+
+// CTAs per SM the pipelined batch kernel of this precision can keep resident
+int mc_batch_pipe_ctas_per_sm(int prec) {
+  int per = 0;
+  const void* fn = prec ? (const void*)mc_batch_pipe_kernel<float> : (const void*)mc_batch_pipe_kernel<double>;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, MC_THREADS, 0) != cudaSuccess) return 0;
+  return per;
 }
