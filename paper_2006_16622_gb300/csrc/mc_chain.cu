@@ -1254,7 +1254,7 @@ __global__ void __launch_bounds__(MC_THREADS, 1)
 // in device memory, step counter advanced in place so that a replayed graph
 // continues every chain's proposal stream
 template <typename TE, int kVar>
-__global__ void __launch_bounds__(MC_THREADS, MC_BATCH_CTAS_PER_SM)
+__global__ void __launch_bounds__(MC_THREADS, MC_BATCH_CTAS_PER_SM(TE))
     mc_batch_kernel(const McSys* const* __restrict__ systems, RunParams* __restrict__ rps,
                     const int* __restrict__ cta_chain, const int* __restrict__ cta_rank,
                     const int* __restrict__ chain_ctas) {
@@ -1341,7 +1341,8 @@ int mc_batch_max_ctas(int prec) {
       return 0;
     best = std::min(best, per);
   }
-  return best < 1 ? 0 : sms * std::min(best, MC_BATCH_CTAS_PER_SM);
+  const int cap = prec ? MC_BATCH_CTAS_PER_SM(float) : MC_BATCH_CTAS_PER_SM(double);
+  return best < 1 ? 0 : sms * std::min(best, cap);
 }
 
 int mc_chain_max_ctas(int prec) {

@@ -911,7 +911,7 @@ __global__ void __launch_bounds__(MC_THREADS, 1)
 }
 
 template <typename TE>
-__global__ void __launch_bounds__(MC_THREADS, MC_BATCH_CTAS_PER_SM)
+__global__ void __launch_bounds__(MC_THREADS, MC_BATCH_CTAS_PER_SM(TE))
     mc_batch_pipe_kernel(const McSys* const* __restrict__ systems, RunParams* __restrict__ rps,
                          const int* __restrict__ cta_chain, const int* __restrict__ cta_rank,
                          const int* __restrict__ chain_ctas) {
