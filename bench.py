@@ -57,6 +57,28 @@ def parse():
     return ap.parse_args()
 
 
+# ------------------------------------------------------- replicas over GPUs
+def replica_seed(base: int, rank: int) -> int:
+    """Seed of the independent chain on GPU `rank` (replicas: no data-path
+    collective; only the timing is reduced)."""
+    return base + 1000 * rank
+
+
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """Largest x over all ranks of the process group (x itself without one)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Units of all ranks over the slowest rank's time."""
+    return world * units_per_rank / seconds_max
+
+
 # ------------------------------------------------------------- CPU oracle leg
 def _oracle_worker(q_out, sample, warm):
     """Runs in a spawned process: oracle setup (untimed), then `sample`
@@ -467,7 +489,7 @@ def gpu_arm(args):
         t0 = time.perf_counter()
         ctx.setup()
         setup_s = time.perf_counter() - t0
-        seed = W.seed + 1000 * rank
+        seed = replica_seed(W.seed, rank)
         for _ in range(args.warmup):
             ctx.run(S, seed=seed, beta=W.beta, half_width=W.half_width, stats=False)
         torch.cuda.synchronize()
@@ -497,11 +519,7 @@ def gpu_arm(args):
         ctx.close()
         if status != 0:
             raise RuntimeError(f"chain status {status}")
-        tot = sum(durs)
-        if dist is not None:
-            t = torch.tensor([tot], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = float(t.item())
+        tot = max_over_ranks(sum(durs), dist, "cuda")
         return dict(total=tot, durs=durs, setup_s=setup_s, nu=nu, clocks=clocks)
 
     r64 = time_form(mcfmm.FP64)
@@ -529,15 +547,15 @@ def gpu_arm(args):
             ctx = mcfmm.Context(pos, q, W.a, W.levels, W.p, precision=mcfmm.FP64,
                                 stream=stream.cuda_stream)
             ctx.setup()
-            ctx.run(S, seed=W.seed + 7 + 1000 * rank, beta=W.beta, half_width=W.half_width,
+            ctx.run(S, seed=replica_seed(W.seed + 7, rank), beta=W.beta, half_width=W.half_width,
                     stats=False)
             out_pos = ctx.positions()
             e = ctx.energy()
             ctx.close()
             t_e2e.append(time.perf_counter() - t0)
             assert np.isfinite(e) and out_pos.shape == pos.shape
-        te = max(t_e2e[1:]) if len(t_e2e) > 1 else t_e2e[0]
-        e2e = {"value": world * S / te, "unit": UNIT,
+        te = max_over_ranks(max(t_e2e[1:]) if len(t_e2e) > 1 else t_e2e[0], dist, "cuda")
+        e2e = {"value": whole_job_rate(S, world, te), "unit": UNIT,
                "h2d_bytes_per_step": int(pos.nbytes + q.nbytes),
                "d2h_bytes_per_step": int(len(q) * 32 + 8),
                "what": "per step: mc_init from host arrays, mc_setup, mc_run, positions + energy "
@@ -545,7 +563,7 @@ def gpu_arm(args):
 
     if rank != 0:
         return
-    value = world * S * args.steps / r64["total"]
+    value = whole_job_rate(S * args.steps, world, r64["total"])
     nbar = W.n / (8 ** (W.levels - 1))
     F, Fp, Fa = algorithmic_flops_per_step(W.p, W.levels, nbar, r64["nu"])
     per_launch = statistics.mean(r64["durs"])
@@ -570,8 +588,8 @@ def gpu_arm(args):
         proc.join(timeout=10)
     forms = {"fp64": value}
     if r32:
-        forms["fp32_eval"] = world * S * args.steps / r32["total"]
-        forms["fp32_eval_plain_schedule"] = world * S * args.steps / r32p["total"]
+        forms["fp32_eval"] = whole_job_rate(S * args.steps, world, r32["total"])
+        forms["fp32_eval_plain_schedule"] = whole_job_rate(S * args.steps, world, r32p["total"])
         forms["fp32_eval_acceptance"] = r32["nu"]
         forms["fp32_eval_setup_s"] = r32["setup_s"]
     if sweep:
