@@ -221,6 +221,64 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
   int pf_j = 0;
   double pf_d = 0.0, pf_u = 0.5;
   double4 pf_pos = make_double4(0, 0, 0, 0);
+  // geometry of a proposal (warp 0, per lane: r, r' components on lanes
+  // 0..2; the offsets from the cell centres for side lane/16, level slot
+  // lane%16), formed for the next step at the end of this step's items
+  struct PGeo {
+    int j, cf, cfn, lo;
+    double q, uu, r, rn;
+    double off[3];
+    bool out;
+  } pg;
+  pg.j = -1;
+  pg.lo = 0;
+  bool pg_ok = false;
+  // whole warp: j, charge (lanes 0..2), r and d (or r' when !is_d) per axis lane
+  auto form_geo = [&](PGeo& G, int j, double q, double r, double dn, bool is_d, double uu) {
+    double rn = 0.0;
+    bool out = false;
+    if (lane < 3) {
+      if (is_d) {
+        double x = __dadd_rn(r, dn);
+        if (pbc) {
+          if (x < 0.0) x = __dadd_rn(x, S.a);
+          if (x >= S.a) x = __dsub_rn(x, S.a);
+        } else if (!(x >= 0.0 && x < S.a)) {
+          out = true;
+        }
+        rn = x;
+      } else {
+        rn = dn;
+      }
+    }
+    const bool any_out = __any_sync(0xffffffffu, lane < 3 && out);
+    int cf = 0, cfn = 0;
+    if (lane < 3) {
+      cf = finest_coord(r, S.inv_wL, S.nL);
+      cfn = any_out ? cf : finest_coord(rn, S.inv_wL, S.nL);
+    }
+    const int side = lane >> 4, li = lane & 15;
+    const int l = L - li;
+    const int lo = (l >= 1 && l <= L && li <= L - 1) ? l : 0;
+#pragma unroll
+    for (int ax = 0; ax < 3; ax++) {
+      const double xo = __shfl_sync(0xffffffffu, r, ax), xn = __shfl_sync(0xffffffffu, rn, ax);
+      const int co = __shfl_sync(0xffffffffu, cf, ax), cnn = __shfl_sync(0xffffffffu, cfn, ax);
+      const double xs = side ? xn : xo;
+      const int cs = side ? cnn : co;
+      G.off[ax] = lo ? xs - ((double)(cs >> (L - lo)) + 0.5) * S.lev_w[lo] : 0.0;
+    }
+    G.j = j;
+    G.q = __shfl_sync(0xffffffffu, q, 0);
+    G.uu = uu;
+    G.r = r;
+    G.rn = rn;
+    G.cf = cf;
+    G.cfn = cfn;
+    G.lo = lo;
+    G.out = any_out;
+  };
+
   // the two previous steps (every thread): moved, particle; warp 0 lanes
   // 0..2 also keep their r' components.  The accept of a step can still be
   // running in other CTAs when this CTA reads ahead (see the split barrier
@@ -237,95 +295,65 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
     if (prof_lead) tp0 = mc_globaltimer();
     // ------------------------------------------------------------ proposal
     if (warp == 0) {
-      int j;
-      double q = 0.0, uu = 0.5, r = 0.0, rn = 0.0;
-      bool out = false;
       if (rp.mode == 0) {
-        double d = 0.0;
-        double4 pj;
-        if (pf_ok) {
-          j = pf_j;
-          d = pf_d;
-          uu = pf_u;
-          pj = pf_pos;
-        } else {
-          mc_proposal_axis(rp.seed, (unsigned long long)(rp.step0 + t), rp.chain, S.n, rp.h,
-                           lane < 3 ? lane : 0, &j, &d, lane == 3 ? &uu : nullptr);
-          pj = lane < 3 ? ldcg4(&S.ppos[j]) : make_double4(0, 0, 0, 0);
-        }
-        if (lane < 3) {
-          q = pj.w;
-          r = lane == 0 ? pj.x : (lane == 1 ? pj.y : pj.z);
-          // a prefetched load may predate the accept of one of the two
-          // previous steps: if one of them moved this particle, the latest
-          // such r' is its position
+        // the geometry formed at the end of the previous step holds unless
+        // one of the two previous steps moved this particle (the position was
+        // loaded before their accepts); else form it again here
+        const bool fast = pg_ok && !(mv1 && pg.j == j1) && !(mv2 && pg.j == j2);
+        if (!fast) {
+          int j;
+          double d = 0.0, uu = 0.5;
+          double4 pj;
           if (pf_ok) {
+            j = pf_j;
+            d = pf_d;
+            uu = pf_u;
+            pj = pf_pos;
+          } else {
+            mc_proposal_axis(rp.seed, (unsigned long long)(rp.step0 + t), rp.chain, S.n, rp.h,
+                             lane < 3 ? lane : 0, &j, &d, lane == 3 ? &uu : nullptr);
+            pj = lane < 3 ? ldcg4(&S.ppos[j]) : make_double4(0, 0, 0, 0);
+          }
+          double r = lane == 0 ? pj.x : (lane == 1 ? pj.y : pj.z);
+          if (pf_ok && lane < 3) {
             if (mv1 && j == j1) {
               r = rn1;
             } else if (mv2 && j == j2) {
               r = rn2;
             }
           }
-          double x = __dadd_rn(r, d);
-          if (pbc) {
-            if (x < 0.0) x = __dadd_rn(x, S.a);
-            if (x >= S.a) x = __dsub_rn(x, S.a);
-          } else if (!(x >= 0.0 && x < S.a)) {
-            out = true;
-          }
-          rn = x;
+          form_geo(pg, j, pj.w, r, d, true, uu);
         }
       } else {
-        j = (int)rp.jg;
-        if (lane < 3) {
-          const double4 pj = ldcg4(&S.ppos[j]);
-          q = pj.w;
-          r = lane == 0 ? pj.x : (lane == 1 ? pj.y : pj.z);
-          rn = lane == 0 ? rp.rx : (lane == 1 ? rp.ry : rp.rz);
-        }
+        const int j = (int)rp.jg;
+        const double4 pj = lane < 3 ? ldcg4(&S.ppos[j]) : make_double4(0, 0, 0, 0);
+        const double r = lane == 0 ? pj.x : (lane == 1 ? pj.y : pj.z);
+        const double rn = lane == 0 ? rp.rx : (lane == 1 ? rp.ry : rp.rz);
+        form_geo(pg, j, pj.w, r, rn, false, 0.5);
       }
-      const bool any_out = __any_sync(0xffffffffu, lane < 3 && out);
-      int cf = 0, cfn = 0;
-      if (lane < 3) {
-        cf = finest_coord(r, S.inv_wL, S.nL);
-        cfn = any_out ? cf : finest_coord(rn, S.inv_wL, S.nL);
-      }
-      // sgeo of the previous step is read above; all lanes have passed that
-      // point once the shuffles below have run
-      // offsets from the cell centres: lane = side * 16 + level-slot, axis loop
-      double offv[3];
-      int lo = 0;
-      {
-        const int side = lane >> 4, li = lane & 15;
-        const int l = L - li;
-        lo = (l >= 1 && l <= L && li <= L - 1) ? l : 0;
-#pragma unroll
-        for (int ax = 0; ax < 3; ax++) {
-          const double xo = __shfl_sync(0xffffffffu, r, ax), xn = __shfl_sync(0xffffffffu, rn, ax);
-          const int co = __shfl_sync(0xffffffffu, cf, ax), cnn = __shfl_sync(0xffffffffu, cfn, ax);
-          const double xs = side ? xn : xo;
-          const int cs = side ? cnn : co;
-          offv[ax] = lo ? xs - ((double)(cs >> (L - lo)) + 0.5) * S.lev_w[lo] : 0.0;
-        }
-      }
-      __syncwarp();
-      if (lo) {
+      // publish
+      if (pg.lo) {
         const int side = lane >> 4;
 #pragma unroll
-        for (int ax = 0; ax < 3; ax++) s_off[side][lo][ax] = offv[ax];
+        for (int ax = 0; ax < 3; ax++) s_off[side][pg.lo][ax] = pg.off[ax];
       }
       if (lane < 3) {
-        sgeo.r[lane] = r;
-        sgeo.rn[lane] = rn;
-        sgeo.cf[lane] = cf;
-        sgeo.cfn[lane] = cfn;
+        sgeo.r[lane] = pg.r;
+        sgeo.rn[lane] = pg.rn;
+        sgeo.cf[lane] = pg.cf;
+        sgeo.cfn[lane] = pg.cfn;
       }
       if (lane == 0) {
-        sgeo.j = j;
-        sgeo.q = q;
-        sgeo.outside = any_out;
+        sgeo.j = pg.j;
+        sgeo.q = pg.q;
+        sgeo.outside = pg.out;
       }
-      if (lane == 3) s_u = uu;
+      if (lane == 3) s_u = pg.uu;
+      pg_ok = false;
+    }
+    __syncthreads();
+    const StepGeo g = sgeo;
+    if (warp == 0) {
       // draw the next proposal and start loading its particle
       pf_ok = false;
       if (rp.mode == 0 && t + 1 < rp.nsteps) {
@@ -335,8 +363,6 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
         pf_ok = true;
       }
     }
-    __syncthreads();
-    const StepGeo g = sgeo;
     const double u = s_u;
     const bool nomove = (g.r[0] == g.rn[0] && g.r[1] == g.rn[1] && g.r[2] == g.rn[2]);
     const bool same = (g.cf[0] == g.cfn[0] && g.cf[1] == g.cfn[1] && g.cf[2] == g.cfn[2]);
@@ -856,6 +882,12 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
         part[it] = partial;
       }
       if (prof_on && lane == 0) prof_item(rp.prof, ptype, t_item);
+    }
+    if (warp == 0 && pf_ok) {
+      // the next proposal's geometry, while the other items still run
+      form_geo(pg, pf_j, pf_pos.w, lane == 0 ? pf_pos.x : (lane == 1 ? pf_pos.y : pf_pos.z), pf_d,
+               true, pf_u);
+      pg_ok = true;
     }
     if (mm) {
       // the multipole method has more items than partial slots: one partial
