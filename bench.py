@@ -228,9 +228,10 @@ def bytes_per_step(p, levels, nbar, nu):
 
 
 def read_profile_traffic():
-    """DRAM bytes per launch of the timed chain kernel (50 000 proposals) from
-    the committed ncu summary of one full launch, or None."""
-    path = os.path.join(ROOT, "profiles", "chain_fp64_dram_full_launch_N1e5.md")
+    """DRAM bytes per launch of the timed chain kernel (the barrier-free FP64
+    chain, 50 000 proposals) from the committed ncu summary of one full
+    launch, or None."""
+    path = os.path.join(ROOT, "profiles", "async_fp64_dram_full_launch_N1e5.md")
     try:
         for line in open(path):
             if line.startswith("dram_bytes_per_launch:"):
@@ -481,10 +482,13 @@ def gpu_arm(args):
     S = args.mh_steps
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def time_form(precision, schedule=mcfmm.SCHEDULE_PHASED):
+    def time_form(precision, schedule=None):
+        # schedule None: the context's default (barrier-free for FP64,
+        # phased for FP32-eval)
         ctx = mcfmm.Context(pos, q, W.a, W.levels, W.p, precision=precision,
                             stream=stream.cuda_stream)
-        ctx.set_schedule(schedule)
+        if schedule is not None:
+            ctx.set_schedule(schedule)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx.setup()
@@ -523,8 +527,9 @@ def gpu_arm(args):
         return dict(total=tot, durs=durs, setup_s=setup_s, nu=nu, clocks=clocks)
 
     r64 = time_form(mcfmm.FP64)
-    r32 = r32p = None
+    r64p = r32 = r32p = None
     if not args.no_fp32:
+        r64p = time_form(mcfmm.FP64, mcfmm.SCHEDULE_PHASED)
         r32 = time_form(mcfmm.FP32_EVAL)
         r32p = time_form(mcfmm.FP32_EVAL, mcfmm.SCHEDULE_PLAIN)
 
@@ -572,7 +577,7 @@ def gpu_arm(args):
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
             "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_FLOPS,
             "traffic": traffic_launch,
-            "kernel": "mc_chain_kernel<double>",
+            "kernel": "mc_async_kernel<double>",
             "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (recipe unit counts)",
             "flops_per_mh_step": F, "bytes_per_mh_step": bytes_per_step(W.p, W.levels, nbar, r64["nu"]),
             "acceptance": r64["nu"]}
@@ -588,6 +593,7 @@ def gpu_arm(args):
         proc.join(timeout=10)
     forms = {"fp64": value}
     if r32:
+        forms["fp64_phased_schedule"] = whole_job_rate(S * args.steps, world, r64p["total"])
         forms["fp32_eval"] = whole_job_rate(S * args.steps, world, r32["total"])
         forms["fp32_eval_plain_schedule"] = whole_job_rate(S * args.steps, world, r32p["total"])
         forms["fp32_eval_acceptance"] = r32["nu"]
@@ -613,7 +619,8 @@ def gpu_arm(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": W.name, "mh_steps_per_step": S, "form": "fp64",
-                       "schedule": "phased (speculative accept contributions)",
+                       "schedule": "barrier-free (MC_SCHEDULE_ASYNC)",
+                       "fp32_eval_schedule": "phased (speculative accept contributions)",
                        "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,

@@ -142,7 +142,7 @@ int mc_get_multipole(mc_ctx *ctx, int level, double *out);
  * complex interleaved, index 2*(l*l + l + m). */
 int mc_lattice_sums(int lmax, double *out);
 /* Schedule of mc_run / mc_batch_run chains.
- *   MC_SCHEDULE_PHASED     (default for mc_run) propose items, grid barrier,
+ *   MC_SCHEDULE_PHASED     (default for FP32-eval contexts) propose items, grid barrier,
  *                          decision, accept items, grid barrier: two barriers
  *                          per accepted step.  The Alg. L.2 contributions of
  *                          the proposed move are computed during the
@@ -157,10 +157,21 @@ int mc_lattice_sums(int lmax, double *out);
  *                          far (contention of the merged phase);
  *   MC_SCHEDULE_PLAIN      (default for FP32-eval batches) as PHASED, with
  *                          the Alg. L.2 contributions computed after the
- *                          decision (no work on rejected moves). */
+ *                          decision (no work on rejected moves);
+ *   MC_SCHEDULE_ASYNC      (default for FP64 contexts) no barrier inside the
+ *                          step loop: warps meet through per-step partial
+ *                          slots and counters; the geometry of step k+1 is
+ *                          published before the decision of step k (unless
+ *                          both draw the same particle), so its speculative
+ *                          Alg. L.2 contributions and far-field change run
+ *                          while step k is decided and applied.  Same results
+ *                          to roundoff.  mc_run chains of the local method
+ *                          only; single proposals (mc_propose, mc_accept) and
+ *                          the multipole method run phased. */
 #define MC_SCHEDULE_PHASED 0
 #define MC_SCHEDULE_PIPELINED 1
 #define MC_SCHEDULE_PLAIN 2
+#define MC_SCHEDULE_ASYNC 3
 int mc_set_schedule(mc_ctx *ctx, int schedule);
 /* Status of the last asynchronous launch (MC_OK, MC_ERR_TIMEOUT, ...). */
 int mc_status(mc_ctx *ctx);
@@ -177,13 +188,19 @@ int mc_inject_wait_fault(mc_ctx *ctx, int missing_arrivals);
 /* Diagnostics: with profiling on, mc_run accumulates MC_PROF_COUNTERS device
  * timers (globaltimer nanoseconds) of its persistent launch: [0..4] CTA 0's
  * own propose items, first barrier wait, decision, own accept items, second
- * barrier wait; [5] proposals, [6] accepts; [8+t], [24+t], [40+t] summed
+ * barrier wait (MC_SCHEDULE_ASYNC: [0] publication of a step's geometry to
+ * its decision, [1] publication to the start of the decision's poll);
+ * [5] proposals, [6] accepts; [8+t], [24+t], [40+t] summed
  * duration, count and maximum of work items of type t (0 expansion
  * evaluation, 1 near cell, 2 far lattice block, 3 image/dipole term,
  * 4 small-level accept entry or apply, 5 accept target cell or apply,
  * 6 bookkeeping and K/H, 7 speculative small-level contribution,
- * 8 speculative large-level contribution).  mc_profile_read copies them
- * (out: MC_PROF_COUNTERS uint64) and clears them. */
+ * 8 speculative large-level contribution; MC_SCHEDULE_ASYNC also, as times
+ * from the publication of the item's step: 9 expansion item's state ready,
+ * 10 expansion item done, 11 decision seen by an apply item, 12 its
+ * operands loaded, 13 apply item done, 14 near item's state ready, 15 far /
+ * near / image item done).  mc_profile_read copies them (out:
+ * MC_PROF_COUNTERS uint64) and clears them. */
 #define MC_PROF_COUNTERS 56
 int mc_profile(mc_ctx *ctx, int on);
 int mc_profile_read(mc_ctx *ctx, uint64_t *out);

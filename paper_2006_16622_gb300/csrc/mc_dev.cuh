@@ -60,9 +60,9 @@ struct McSys {
   double* G;         // [C*C] real far-field operator: Hhat = G Khat
   double* dipv;      // [3] dipole sum q r
   double* energy;    // [1] running energy
-  double* partials;  // [2 * MC_MAX_ITEMS]
-  double* dK;        // [2 * C] change of Khat of the current proposal
-  double* gK;        // [2 * MC_NF_COLS * C] partial G dK of the current proposal
+  double* partials;  // [4 * MC_MAX_ITEMS] (two used by the phased kernels, a ring of four by mc_async.cu)
+  double* dK;        // [4 * C] change of Khat of the current proposal (by step: 2 or 4 buffers)
+  double* gK;        // [4 * MC_NF_COLS * C] partial G dK of the current proposal (2 or 4 buffers)
   unsigned long long* bar;  // grid barrier counter
   int* status;       // device status word (MC_OK or MC_ERR_*)
   long long* stats;  // [4] steps, accepted, borderline, spare
@@ -71,13 +71,15 @@ struct McSys {
   // coarse-level deltas (3 rotating buffers of nsmall cells x C), sync words
   double* Hhat2;     // [C]
   double* dipv2;     // [3]
-  double* dsmall;    // [3 * nsmall * C]
+  double* dsmall;    // [4 * nsmall * C] (rotating buffers: three or four)
   int ls_end;        // first level with more than 4 cells per axis (or L + 1)
   int nsmall;        // cells of levels lmin .. ls_end-1 (the first cells of Lhat)
-  unsigned long long* sync;  // [16]: [l] read epoch of level l, [12] near items done
+  unsigned long long* sync;  // [16]: [l] read epoch of level l, [12] near items done;
+                             // mc_async.cu: [0..3] contributions, [4] K item, [5] decisions
   // speculative accept: Alg. L.2 contributions staged during the proposal
-  double* dacc;      // [2 (step parity) * (L - lmin + 1) * MC_DSLOTS * C]
-  double* dKpre;     // [2 * C] dK of the next proposal, by step parity
+  double* dacc;      // [4 (step) * (L - lmin + 1) * 2 * MC_DSLOTS * C] (phased: by step parity;
+                     // mc_async.cu: by step mod 4 and side)
+  double* dKpre;     // [4 * C] dK of the next proposal, by step (2 or 4 buffers)
   // multipole method (Sec. 3.2, alternative algorithm; method 1): per-level
   // scaled multipoles Mhat_n^m = sum q conj Rt_n^m(r - R_cell), Lhat's layout
   int method;
@@ -380,7 +382,7 @@ __device__ __forceinline__ void cmul(T ar, T ai, T br, T bi, T* cr, T* ci) {
   *ci = ar * bi + ai * br;
 }
 
-template <typename T, typename F, bool kUnroll = true>
+template <typename T, typename F, bool kUnroll = true, bool kW = false>
 __device__ __forceinline__ void harm_group(const T (*A)[16], const T (*B)[16], int p, T X, T Y,
                                            T Z, T Q, T start, F&& use) {
   const int g = threadIdx.x & 7;
@@ -431,7 +433,7 @@ __device__ __forceinline__ void harm_group(const T (*A)[16], const T (*B)[16], i
     const bool valid = active && (c1 || two) && n <= p;
     const bool st = (n == m);
     const int nn = n > 15 ? 15 : n;
-    const T a = Z * A[nn][m], b = Q * B[nn][m];
+    const T a = kW ? Z : Z * A[nn][m], b = Q * B[nn][m];
     T vr = a * p1r - b * p2r, vi = a * p1i - b * p2i;
     const T sr = c1 ? d1r : d2r, si = c1 ? d1i : d2i;
     vr = st ? sr : vr;
@@ -504,6 +506,41 @@ __device__ __forceinline__ void irregular_group_s(const HarmTabs<T>* t, int p, T
   const T ir = mc_rsqrt(r2);
   const T ir2 = ir * ir;
   harm_group<T, F, false>(t->iA, t->iB, p, x * ir2, y * ir2, z * ir2, ir2, ir * s, static_cast<F&&>(use));
+}
+
+// Column-scaled irregular sets: below the diagonal, value (n, m) divided by
+// P_n^m = prod_{k=m+1..n} (2k - 1), so the recurrence loses the factor
+// (2n - 1) of its first term (5 instead of 6 flops per step) and its second
+// term takes W[n][m] = ((n-1)^2 - m^2) / ((2n-1)(2n-3)) (irregular_w_tabs).
+// The consumer multiplies by P_n^m (irregular_p), e.g. in the fused
+// multiply-add that adds the value into an expansion.
+template <typename T, typename F>
+__device__ __forceinline__ void irregular_group_w(const HarmTabs<T>* t, const T (*W)[16], int p, T x,
+                                                  T y, T z, T s, F&& use) {
+  const T r2 = x * x + y * y + z * z;
+  const T ir = mc_rsqrt(r2);
+  const T ir2 = ir * ir;
+  harm_group<T, F, false, true>(t->iA, W, p, x * ir2, y * ir2, z * ir2, ir2, ir * s,
+                                static_cast<F&&>(use));
+}
+
+template <typename T>
+__device__ void irregular_w_tabs(T (*W)[16], double* P) {
+  for (int k = threadIdx.x; k < (MC_PMAX + 1) * 16; k += blockDim.x) {
+    const int n = k / 16, m = k % 16;
+    double w = 0.0;
+    if (n >= m + 2) w = ((double)(n - 1) * (n - 1) - (double)m * m) / ((2.0 * n - 1.0) * (2.0 * n - 3.0));
+    W[n][m] = (T)w;
+  }
+  // P_n^m at the real layout index of (n, m) (both parts)
+  for (int k = threadIdx.x; k < (MC_PMAX + 1) * (MC_PMAX + 1); k += blockDim.x) {
+    int n = 0;
+    while ((n + 1) * (n + 1) <= k) n++;
+    const int m = (k == n * n) ? 0 : (k - n * n + 1) / 2;
+    double pr = 1.0;
+    for (int j = m + 1; j <= n; j++) pr *= 2.0 * j - 1.0;
+    P[k] = pr;
+  }
 }
 
 // Column factorisation: every scaled harmonic of column m is the diagonal

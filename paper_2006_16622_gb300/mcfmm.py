@@ -18,7 +18,7 @@ MC_OK = 0
 BC_PBC, BC_FREE = 0, 1
 TINFOIL, VACUUM = 0, 1
 FP64, FP32_EVAL = 0, 1
-SCHEDULE_PHASED, SCHEDULE_PIPELINED, SCHEDULE_PLAIN = 0, 1, 2
+SCHEDULE_PHASED, SCHEDULE_PIPELINED, SCHEDULE_PLAIN, SCHEDULE_ASYNC = 0, 1, 2, 3
 SETUP_P2L, SETUP_FMM, SETUP_MULTIPOLE = 0, 1, 2
 PROF_COUNTERS = 56
 

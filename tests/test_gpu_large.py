@@ -1,7 +1,8 @@
 """Parity at the benchmark's full size and launch configuration.
 
 The N=1e5 workload (density 0.1, a=100, 5 levels, p=12, h=0.3, beta=1) as
-bench.py times it (one persistent launch over all SMs): the oracle sets the
+bench.py times it (one persistent launch over all SMs; the default FP64
+schedule, and the phased one): the oracle sets the
 same system up (about a minute of one host core), then
   - sampled cells of every level's expansions agree within 1e-12,
   - the first 300 proposals of the seed-0 chain agree: every dE within
@@ -52,17 +53,25 @@ def test_large_setup_sampled_cells(large_pair):
 
 
 def test_large_replayed_chain(large_pair):
+    """The default (barrier-free) FP64 schedule, then the phased one from the
+    same initial state, against the same oracle chain."""
     W, g, o, pos, q = large_pair
     steps = 300
-    rg = g.run(steps, seed=W.seed, beta=W.beta, half_width=W.half_width, log=True)
     ro = o.run(steps, seed=W.seed, step0=0, beta=W.beta, half_width=W.half_width)
-    assert ro["n_borderline"] == 0 and rg["borderline"] == 0
-    assert np.array_equal(rg["j"], ro["j"])
-    err = np.abs(rg["dE"] - ro["dE"]) / np.maximum(1.0, np.abs(ro["dE"]))
-    assert np.max(err) <= 1e-10, np.max(err)
-    assert np.array_equal(rg["acc"], ro["acc"])
-    assert np.array_equal(g.positions(), o.positions())
-    assert abs(g.energy() - o.energy()) <= 1e-9 * abs(o.energy())
+    assert ro["n_borderline"] == 0
+    f = mcfmm.Context(pos, q, W.a, W.levels, W.p, precision=mcfmm.FP64)
+    f.setup()
+    f.set_schedule(mcfmm.SCHEDULE_PHASED)
+    for ctx in (g, f):
+        rg = ctx.run(steps, seed=W.seed, beta=W.beta, half_width=W.half_width, log=True)
+        assert rg["borderline"] == 0
+        assert np.array_equal(rg["j"], ro["j"])
+        err = np.abs(rg["dE"] - ro["dE"]) / np.maximum(1.0, np.abs(ro["dE"]))
+        assert np.max(err) <= 1e-10, np.max(err)
+        assert np.array_equal(rg["acc"], ro["acc"])
+        assert np.array_equal(ctx.positions(), o.positions())
+        assert abs(ctx.energy() - o.energy()) <= 1e-9 * abs(o.energy())
+    f.close()
 
 
 def test_large_properties_after_a_long_chain(large_pair):

@@ -26,15 +26,17 @@ def _lib():
     mcfmm.load()
 
 
-@pytest.mark.parametrize("method", ["local", "multipole"])
+@pytest.mark.parametrize("method", ["local", "local-phased", "multipole"])
 def test_lj_chain_replays_oracle(method):
     pos, q, a = perturbed_nacl(8, seed=3)
     L, p = 2, 8
     g = mcfmm.Context(pos, q, a, L, p)
+    if method == "local-phased":
+        g.set_schedule(mcfmm.SCHEDULE_PHASED)
     g.set_lj(NACL_LJ_EPS, NACL_LJ_SIGMA, NACL_LJ_CUTOFF)
     o = O.System(pos, q, a, L, p)
     o.set_lj(NACL_LJ_EPS, NACL_LJ_SIGMA, NACL_LJ_CUTOFF)
-    if method == "local":
+    if method != "multipole":
         g.setup()
         o.setup()
     else:
