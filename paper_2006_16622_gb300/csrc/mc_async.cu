@@ -448,6 +448,13 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
         accept = lu < t2;
         if (fabs(lu - t2) < 1e-9 * fmax(1.0, fabs(t2))) n_border++;
       }
+      // decision ring slot t & 3 last held step t - 4, read by warps up to
+      // their step t - 3 (the decisions before their state waits)
+      if (t >= 3) {
+        for (int w2 = 0; w2 < MC_WARPS && ok; w2++)
+          if (w2 != MC_ASYNC_CTRL) ok = flag_wait(&s_wdone[w2], t - 3, &s_abort, S.status, rp.wait_ns);
+        if (!ok) break;
+      }
       if (accept && !nomove) cumB += (unsigned long long)nB;
       if (lane == 0) {
         s_dEu[gi] = dE;
@@ -502,6 +509,7 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
     // particle and no-move flag of the two previous steps
     int j_prev = -1, j_prev2 = -1;
     bool nomove_prev = true, nomove_prev2 = true;
+    int cf_prev[3] = {0, 0, 0}, cfn_prev[3] = {0, 0, 0};  // finest cells of step t-1's move
     for (long long t = 0;; t++) {
       if (!flag_wait(&s_gstep, t, &s_abort, S.status, rp.wait_ns)) {
         s_abort = 1;
@@ -706,6 +714,13 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
               const TE accn = __shfl_sync(0xffffffffu, acc, 8);
               partial = g.q * to_double(accn - acc);
             }
+            // on a step without a move too: the decision of every step then
+            // implies that the applies of the step before are complete,
+            // which the reuse of the step-indexed buffers relies on
+            if (idle && !need_state()) {
+              fail = true;
+              break;
+            }
             put(slotE + e, partial);
             if (prof_on && lane == 0) {
               prof_item(rp.prof, 0, t_item);
@@ -848,16 +863,12 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
                   }
                 });
               }
-              if (!need_state()) {
-                fail = true;
-                break;
-              }
-              const double hk = (cb == 0 && k < C) ? __ldcg(&S.Hhat[k]) : 0.0;
               __syncwarp();
+              // the block of G dK needs no state; only the first column block
+              // reads H (which the accepts change), after the state wait
               const int cbeg = cb * csz, cend = min(C, cbeg + csz);
-              double contrib = 0.0;
+              double gk = 0.0;
               if (k < C) {
-                double gk = 0.0;
                 if (gpre && it == lw) {
 #pragma unroll
                   for (int i = 0; i < MC_GPRE; i++)
@@ -866,6 +877,17 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
                   for (int c = cbeg; c < cend; c++) gk += __ldcg(&S.G[(size_t)c * C + k]) * st[c];
                 }
                 S.gK[(size_t)(t & 3) * MC_NF_COLS * C + (size_t)cb * C + k] = gk;
+              }
+              double hk = 0.0;
+              if (cb == 0) {
+                if (!need_state()) {
+                  fail = true;
+                  break;
+                }
+                hk = k < C ? __ldcg(&S.Hhat[k]) : 0.0;
+              }
+              double contrib = 0.0;
+              if (k < C) {
                 const double Wk = is_square(k) ? 1.0 : 2.0;
                 contrib = Wk * st[k] * (0.5 * gk + hk);
               }
@@ -901,7 +923,13 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
                 c1 = e1;
                 c2 = e2;
               }
-              if (!need_state()) {
+              // the accept of step t-1 changed the lists of its two finest
+              // cells only (every earlier accept preceded the decision of
+              // step t-1); other cells need no wait
+              const bool touched = s_acc[(t - 1) & 3] != 0 && !nomove_prev &&
+                                   ((c0 == cf_prev[0] && c1 == cf_prev[1] && c2 == cf_prev[2]) ||
+                                    (c0 == cfn_prev[0] && c1 == cfn_prev[1] && c2 == cfn_prev[2]));
+              if (t > 0 && touched && !need_state()) {
                 fail = true;
                 break;
               }
@@ -1217,6 +1245,11 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
       nomove_prev2 = nomove_prev;
       j_prev = g.j;
       nomove_prev = nomove;
+#pragma unroll
+      for (int d = 0; d < 3; d++) {
+        cf_prev[d] = g.cf[d];
+        cfn_prev[d] = g.cfn[d];
+      }
       if (lane == 0) flag_publish(&s_wdone[warp], t);
       __syncwarp();
     }
