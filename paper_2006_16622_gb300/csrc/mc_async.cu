@@ -155,7 +155,9 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
   __shared__ unsigned long long s_tpub[4];  // publication times (profiling)
   __shared__ double s_dEu[4];
   __shared__ int s_acc[4];
-  __shared__ unsigned long long s_cumB[4];  // apply items of the accepted steps through step s
+  // apply items of the accepted steps through step s (ring of 8 by step):
+  // bookkeeping and K/H, small-level cells, large-level targets
+  __shared__ unsigned long long s_cumB[8], s_cumBs[8], s_cumBL[8];
   __shared__ volatile long long s_gstep;  // last published geometry step
   __shared__ volatile long long s_dstep;  // last published decision step
   __shared__ volatile long long s_stop;   // steps of this launch (set when the chain stops)
@@ -329,7 +331,9 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
     double4 pf_pos = make_double4(0, 0, 0, 0);
     long long t = 0;
     bool ok = true;
-    unsigned long long cumB = 0ull;  // apply items of the accepted steps so far
+    // apply items of the accepted steps so far: bookkeeping and K/H (counted
+    // on S.bar), small-level cells (sync[6]), large-level targets (sync[7])
+    unsigned long long cumB = 0ull, cumBs = 0ull, cumBL = 0ull;
     // proposal 0
     {
       double uu = 0.5;
@@ -369,13 +373,17 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
         nDs += it_l;
         if (S.lev_n[l] > 4) nLB2 += it_l;
       }
-      const int nB = 1 + (pbc ? (C + 31) / 32 : 0) + S.nsmall + nLB2;
+      const int nBk = 1 + (pbc ? (C + 31) / 32 : 0);
       // ---- proposal t+1: its position load holds every move up to step
-      //      t-2 (their applies preceded this warp's last decision); the
-      //      decided move of step t-1 is put in here.  Published at once
+      //      t-2 (their bookkeeping is waited for); the decided move of step
+      //      t-1 is put in here.  Published at once
       //      unless it draws the particle of step t, whose move is not
       //      decided yet
       if (t + 1 < rp.nsteps) {
+        if (t >= 2 && !counter_wait(S.bar, s_cumB[(t - 2) & 7], S.status, rp.wait_ns)) {
+          ok = false;
+          break;
+        }
         int j;
         double uu = 0.5;
         draw(t + 1, &j, &pf_d, &uu, &pf_pos);
@@ -455,11 +463,17 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
           if (w2 != MC_ASYNC_CTRL) ok = flag_wait(&s_wdone[w2], t - 3, &s_abort, S.status, rp.wait_ns);
         if (!ok) break;
       }
-      if (accept && !nomove) cumB += (unsigned long long)nB;
+      if (accept && !nomove) {
+        cumB += (unsigned long long)nBk;
+        cumBs += (unsigned long long)S.nsmall;
+        cumBL += (unsigned long long)nLB2;
+      }
       if (lane == 0) {
         s_dEu[gi] = dE;
         s_acc[gi] = accept ? 1 : 0;
-        s_cumB[gi] = cumB;
+        s_cumB[t & 7] = cumB;
+        s_cumBs[t & 7] = cumBs;
+        s_cumBL[t & 7] = cumBL;
         flag_publish(&s_dstep, t);
         red_release_add(decdone, 1ull);
         if (cta == 0) {
@@ -550,14 +564,53 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
             halt = true;
             return false;
           }
-          pend = s_cumB[(t - 1) & 3];
+          pend = s_cumB[(t - 1) & 7];
           have_prev = true;
         }
         return true;
       };
+      // bookkeeping and K/H of the accepted steps through t-1 (cell lists,
+      // positions, dipole, K, H)
       auto need_state = [&]() -> bool {
         if (!sync_prev()) return false;
         return pend == 0ull || counter_wait(S.bar, pend, S.status, rp.wait_ns);
+      };
+      // a count ring value of step s (s >= 0; decision s already published)
+      auto cum_at = [&](const unsigned long long* ring, long long st) -> unsigned long long {
+        return st < 0 ? 0ull : ring[st & 7];
+      };
+      // expansions: small-level applies through step t-1; large-level
+      // applies through t-2, and through t-1 when that step's accept wrote
+      // cell c3 of level l (IL(alpha) or IL(alpha') of its move)
+      auto need_small = [&](long long upto) -> bool {
+        const unsigned long long tg = cum_at(s_cumBs, upto);
+        return tg == 0ull || counter_wait(&S.sync[6], tg, S.status, rp.wait_ns);
+      };
+      auto need_large = [&](long long upto) -> bool {
+        const unsigned long long tg = cum_at(s_cumBL, upto);
+        return tg == 0ull || counter_wait(&S.sync[7], tg, S.status, rp.wait_ns);
+      };
+      auto targeted = [&](int l, const int* c3) -> bool {
+        const int nl = S.lev_n[l], sh = L - l;
+        const int co[3] = {cf_prev[0] >> sh, cf_prev[1] >> sh, cf_prev[2] >> sh};
+        const int cn[3] = {cfn_prev[0] >> sh, cfn_prev[1] >> sh, cfn_prev[2] >> sh};
+        int o[3];
+        list_offset(c3, co, nl, pbc, o);
+        if (in_il(o[0], o[1], o[2], co[0], co[1], co[2])) return true;
+        list_offset(c3, cn, nl, pbc, o);
+        return in_il(o[0], o[1], o[2], cn[0], cn[1], cn[2]);
+      };
+      // the expansion rows of level l at the cells of r and r'
+      auto e_wait = [&](int l) -> bool {
+        if (!sync_prev()) return false;
+        if (S.lev_n[l] <= 4) return need_small(t - 1);  // every small cell is written
+        if (!need_large(t - 2)) return false;
+        const bool mv1 = t >= 1 && s_acc[(t - 1) & 3] != 0 && !nomove_prev;
+        if (!mv1) return true;
+        const int sh = L - l;
+        const int cold[3] = {g.cf[0] >> sh, g.cf[1] >> sh, g.cf[2] >> sh};
+        const int cnew[3] = {g.cfn[0] >> sh, g.cfn[1] >> sh, g.cfn[2] >> sh};
+        return (targeted(l, cold) || targeted(l, cnew)) ? need_large(t - 1) : true;
       };
       // staged contributions: by step mod 4, level and side, MC_DSLOTS x C
       auto dslot = [&](int l, int slot, int side) -> double* {
@@ -598,7 +651,7 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
               // move the particle)
               if (t >= 2) {
                 if (!flag_wait(&s_dstep, t - 2, &s_abort, S.status, rp.wait_ns) ||
-                    !counter_wait(S.bar, s_cumB[(t - 2) & 3], S.status, rp.wait_ns)) {
+                    !counter_wait(S.bar, s_cumB[(t - 2) & 7], S.status, rp.wait_ns)) {
                   fail = true;
                   break;
                 }
@@ -680,7 +733,7 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
 #pragma unroll
               for (int i = 0; i < kQ; i++)
                 qq[i] = qd == 0 ? qsv[i] : (qd == 1 ? qsv[kQ + i] : (qd == 2 ? qsv[2 * kQ + i] : qsv[3 * kQ + i]));
-              if (!need_state()) {
+              if (!e_wait(l)) {
                 fail = true;
                 break;
               }
@@ -715,9 +768,9 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
               partial = g.q * to_double(accn - acc);
             }
             // on a step without a move too: the decision of every step then
-            // implies that the applies of the step before are complete,
-            // which the reuse of the step-indexed buffers relies on
-            if (idle && !need_state()) {
+            // implies that the small-level applies of the step before are
+            // complete, which the reuse of their buffers relies on
+            if (idle && !e_wait(L - lv)) {
               fail = true;
               break;
             }
@@ -738,6 +791,12 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
           const int co[3] = {g.cf[0] >> sh, g.cf[1] >> sh, g.cf[2] >> sh};
           const int cn[3] = {g.cfn[0] >> sh, g.cfn[1] >> sh, g.cfn[2] >> sh};
           const int grp = lane >> 3, side = grp & 1;
+          // the staged slots of step t - 4 (same buffer) are read by that
+          // step's large-level applies: complete before they are rewritten
+          if (nl > 4 && t >= 4 && !need_large(t - 4)) {
+            fail = true;
+            break;
+          }
           if (nl <= 4) {
             // entries 2k, 2k+1 of both lists, added into this step's
             // small-level buffer (image copies make targets repeat)
@@ -929,7 +988,8 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
               const bool touched = s_acc[(t - 1) & 3] != 0 && !nomove_prev &&
                                    ((c0 == cf_prev[0] && c1 == cf_prev[1] && c2 == cf_prev[2]) ||
                                     (c0 == cfn_prev[0] && c1 == cfn_prev[1] && c2 == cfn_prev[2]));
-              if (t > 0 && touched && !need_state()) {
+              if ((t >= 2 && !counter_wait(S.bar, cum_at(s_cumB, t - 2), S.status, rp.wait_ns)) ||
+                  (t > 0 && touched && !need_state())) {
                 fail = true;
                 break;
               }
@@ -1077,7 +1137,8 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
             bool own[2] = {false, false};
             int lsm = 0;  // large level of the item (0: small level)
             if (a >= 0) {
-              if (!counter_wait(&dcnt[t & 3], cumD[t & 3], S.status, rp.wait_ns) || !need_state()) {
+              if (!counter_wait(&dcnt[t & 3], cumD[t & 3], S.status, rp.wait_ns) || !sync_prev() ||
+                  !(a < S.nsmall ? need_small(t - 1) : need_large(t - 1))) {
                 fail = true;
                 break;
               }
@@ -1131,6 +1192,11 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
                   }
                 }
               }
+            }
+            // bookkeeping and K/H: after those of the step before
+            if (a < 0 && !need_state()) {
+              fail = true;
+              break;
             }
             if (!decided) {
               if (!flag_wait(&s_dstep, t, &s_abort, S.status, rp.wait_ns)) {
@@ -1229,7 +1295,9 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
               }
             }
             __syncwarp();
-            if (lane == 0) red_release_add(S.bar, 1ull);
+            // arrival: bookkeeping and K/H, small-level cells and large-level
+            // targets on their own counters
+            if (lane == 0) red_release_add(a < 0 ? S.bar : &S.sync[a < S.nsmall ? 6 : 7], 1ull);
             if (prof_on && lane == 0) {
               prof_item(rp.prof, ptype, t_item);
               prof_item(rp.prof, 13, s_tpub[gi]);
