@@ -153,11 +153,11 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
   __shared__ double s_off[4][2][MC_MAXLEV + 2][3];
   __shared__ double s_u[4];
   __shared__ unsigned long long s_tpub[4];  // publication times (profiling)
-  __shared__ double s_dEu[4];
-  __shared__ int s_acc[4];
-  // apply items of the accepted steps through step s (ring of 8 by step):
-  // bookkeeping and K/H, small-level cells, large-level targets
-  __shared__ unsigned long long s_cumB[8], s_cumBs[8], s_cumBL[8];
+  // decision ring, 8 deep: a warp reads decisions of its steps t-2..t, and
+  // no warp is more than 4 steps behind a published geometry
+  __shared__ double s_dEu[8];
+  __shared__ int s_acc[8];
+  __shared__ unsigned long long s_cumB[8];  // apply items of the accepted steps through step s
   __shared__ volatile long long s_gstep;  // last published geometry step
   __shared__ volatile long long s_dstep;  // last published decision step
   __shared__ volatile long long s_stop;   // steps of this launch (set when the chain stops)
@@ -208,9 +208,11 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
   const int lw = (warp - MC_ASYNC_HEAVY - 1) * nCTA + cta;
   const int bstart = nLw - 1 - lw;  // first apply item of a light warp
   const size_t nsC = (size_t)S.nsmall * C;
-  unsigned long long* dcnt = S.sync;         // [0..3]: contributions done, by step mod 4
-  unsigned long long* ktag = S.sync + 4;     // K item of step s done: s + 1
-  unsigned long long* decdone = S.sync + 5;  // decisions made (all CTAs)
+  // counters on their own 128-byte lines (sync[16 i]): [1..4] contributions
+  // done by step mod 4, [5] K item of step s done (s + 1), [6] decisions made
+  unsigned long long* dcnt = S.sync + 16;      // dcnt[16 i]: step mod 4 = i
+  unsigned long long* ktag = S.sync + 16 * 5;
+  unsigned long long* decdone = S.sync + 16 * 6;
 
   // far operator columns kept in registers by the light warp of F item lw
   const bool gpre = nF <= nLw && csz <= MC_GPRE;
@@ -331,9 +333,7 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
     double4 pf_pos = make_double4(0, 0, 0, 0);
     long long t = 0;
     bool ok = true;
-    // apply items of the accepted steps so far: bookkeeping and K/H (counted
-    // on S.bar), small-level cells (sync[6]), large-level targets (sync[7])
-    unsigned long long cumB = 0ull, cumBs = 0ull, cumBL = 0ull;
+    unsigned long long cumB = 0ull;  // apply items of the accepted steps so far
     // proposal 0
     {
       double uu = 0.5;
@@ -373,17 +373,13 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
         nDs += it_l;
         if (S.lev_n[l] > 4) nLB2 += it_l;
       }
-      const int nBk = 1 + (pbc ? (C + 31) / 32 : 0);
+      const int nB = 1 + (pbc ? (C + 31) / 32 : 0) + S.nsmall + nLB2;
       // ---- proposal t+1: its position load holds every move up to step
-      //      t-2 (their bookkeeping is waited for); the decided move of step
-      //      t-1 is put in here.  Published at once
+      //      t-2 (their applies preceded this warp's last decision); the
+      //      decided move of step t-1 is put in here.  Published at once
       //      unless it draws the particle of step t, whose move is not
       //      decided yet
       if (t + 1 < rp.nsteps) {
-        if (t >= 2 && !counter_wait(S.bar, s_cumB[(t - 2) & 7], S.status, rp.wait_ns)) {
-          ok = false;
-          break;
-        }
         int j;
         double uu = 0.5;
         draw(t + 1, &j, &pf_d, &uu, &pf_pos);
@@ -421,7 +417,7 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
             const unsigned long long bb = ld_relaxed_b64(&part[MC_MAX_ITEMS - 1]);
             all = all && (bb != kSentinel);
             lu = __longlong_as_double((long long)bb);
-            if (t > 0) all = all && (ld_relaxed_b64(&dcnt[(t - 1) & 3]) >= dprev);
+            if (t > 0) all = all && (ld_relaxed_b64(&dcnt[16 * ((t - 1) & 3)]) >= dprev);
             if (rp.bar_missing) all = false;  // failure-path test: never complete
           }
           if (__all_sync(0xffffffffu, all)) break;
@@ -456,24 +452,11 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
         accept = lu < t2;
         if (fabs(lu - t2) < 1e-9 * fmax(1.0, fabs(t2))) n_border++;
       }
-      // decision ring slot t & 3 last held step t - 4, read by warps up to
-      // their step t - 3 (the decisions before their state waits)
-      if (t >= 3) {
-        for (int w2 = 0; w2 < MC_WARPS && ok; w2++)
-          if (w2 != MC_ASYNC_CTRL) ok = flag_wait(&s_wdone[w2], t - 3, &s_abort, S.status, rp.wait_ns);
-        if (!ok) break;
-      }
-      if (accept && !nomove) {
-        cumB += (unsigned long long)nBk;
-        cumBs += (unsigned long long)S.nsmall;
-        cumBL += (unsigned long long)nLB2;
-      }
+      if (accept && !nomove) cumB += (unsigned long long)nB;
       if (lane == 0) {
-        s_dEu[gi] = dE;
-        s_acc[gi] = accept ? 1 : 0;
+        s_dEu[t & 7] = dE;
+        s_acc[t & 7] = accept ? 1 : 0;
         s_cumB[t & 7] = cumB;
-        s_cumBs[t & 7] = cumBs;
-        s_cumBL[t & 7] = cumBL;
         flag_publish(&s_dstep, t);
         red_release_add(decdone, 1ull);
         if (cta == 0) {
@@ -523,7 +506,6 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
     // particle and no-move flag of the two previous steps
     int j_prev = -1, j_prev2 = -1;
     bool nomove_prev = true, nomove_prev2 = true;
-    int cf_prev[3] = {0, 0, 0}, cfn_prev[3] = {0, 0, 0};  // finest cells of step t-1's move
     for (long long t = 0;; t++) {
       if (!flag_wait(&s_gstep, t, &s_abort, S.status, rp.wait_ns)) {
         s_abort = 1;
@@ -569,48 +551,9 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
         }
         return true;
       };
-      // bookkeeping and K/H of the accepted steps through t-1 (cell lists,
-      // positions, dipole, K, H)
       auto need_state = [&]() -> bool {
         if (!sync_prev()) return false;
         return pend == 0ull || counter_wait(S.bar, pend, S.status, rp.wait_ns);
-      };
-      // a count ring value of step s (s >= 0; decision s already published)
-      auto cum_at = [&](const unsigned long long* ring, long long st) -> unsigned long long {
-        return st < 0 ? 0ull : ring[st & 7];
-      };
-      // expansions: small-level applies through step t-1; large-level
-      // applies through t-2, and through t-1 when that step's accept wrote
-      // cell c3 of level l (IL(alpha) or IL(alpha') of its move)
-      auto need_small = [&](long long upto) -> bool {
-        const unsigned long long tg = cum_at(s_cumBs, upto);
-        return tg == 0ull || counter_wait(&S.sync[6], tg, S.status, rp.wait_ns);
-      };
-      auto need_large = [&](long long upto) -> bool {
-        const unsigned long long tg = cum_at(s_cumBL, upto);
-        return tg == 0ull || counter_wait(&S.sync[7], tg, S.status, rp.wait_ns);
-      };
-      auto targeted = [&](int l, const int* c3) -> bool {
-        const int nl = S.lev_n[l], sh = L - l;
-        const int co[3] = {cf_prev[0] >> sh, cf_prev[1] >> sh, cf_prev[2] >> sh};
-        const int cn[3] = {cfn_prev[0] >> sh, cfn_prev[1] >> sh, cfn_prev[2] >> sh};
-        int o[3];
-        list_offset(c3, co, nl, pbc, o);
-        if (in_il(o[0], o[1], o[2], co[0], co[1], co[2])) return true;
-        list_offset(c3, cn, nl, pbc, o);
-        return in_il(o[0], o[1], o[2], cn[0], cn[1], cn[2]);
-      };
-      // the expansion rows of level l at the cells of r and r'
-      auto e_wait = [&](int l) -> bool {
-        if (!sync_prev()) return false;
-        if (S.lev_n[l] <= 4) return need_small(t - 1);  // every small cell is written
-        if (!need_large(t - 2)) return false;
-        const bool mv1 = t >= 1 && s_acc[(t - 1) & 3] != 0 && !nomove_prev;
-        if (!mv1) return true;
-        const int sh = L - l;
-        const int cold[3] = {g.cf[0] >> sh, g.cf[1] >> sh, g.cf[2] >> sh};
-        const int cnew[3] = {g.cfn[0] >> sh, g.cfn[1] >> sh, g.cfn[2] >> sh};
-        return (targeted(l, cold) || targeted(l, cnew)) ? need_large(t - 1) : true;
       };
       // staged contributions: by step mod 4, level and side, MC_DSLOTS x C
       auto dslot = [&](int l, int slot, int side) -> double* {
@@ -733,7 +676,7 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
 #pragma unroll
               for (int i = 0; i < kQ; i++)
                 qq[i] = qd == 0 ? qsv[i] : (qd == 1 ? qsv[kQ + i] : (qd == 2 ? qsv[2 * kQ + i] : qsv[3 * kQ + i]));
-              if (!e_wait(l)) {
+              if (!need_state()) {
                 fail = true;
                 break;
               }
@@ -767,10 +710,10 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
               const TE accn = __shfl_sync(0xffffffffu, acc, 8);
               partial = g.q * to_double(accn - acc);
             }
-            // on a step without a move too: the decision of every step then
-            // implies that the small-level applies of the step before are
-            // complete, which the reuse of their buffers relies on
-            if (idle && !e_wait(L - lv)) {
+            // on a step without a move too: decision t then implies that
+            // every apply of step t-1 is complete, which the reuse of the
+            // step-indexed buffers relies on
+            if (idle && !need_state()) {
               fail = true;
               break;
             }
@@ -791,12 +734,6 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
           const int co[3] = {g.cf[0] >> sh, g.cf[1] >> sh, g.cf[2] >> sh};
           const int cn[3] = {g.cfn[0] >> sh, g.cfn[1] >> sh, g.cfn[2] >> sh};
           const int grp = lane >> 3, side = grp & 1;
-          // the staged slots of step t - 4 (same buffer) are read by that
-          // step's large-level applies: complete before they are rewritten
-          if (nl > 4 && t >= 4 && !need_large(t - 4)) {
-            fail = true;
-            break;
-          }
           if (nl <= 4) {
             // entries 2k, 2k+1 of both lists, added into this step's
             // small-level buffer (image copies make targets repeat)
@@ -864,7 +801,7 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
             });
           }
           __syncwarp();
-          if (lane == 0) red_release_add(&dcnt[t & 3], 1ull);
+          if (lane == 0) red_release_add(&dcnt[16 * (t & 3)], 1ull);
           if (prof_on && lane == 0) prof_item(rp.prof, nl <= 4 ? 7 : 8, t_item);
         }
       } else if (light) {
@@ -895,8 +832,8 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
             const int k = rb * 32 + lane;
             // dK formed one step ahead holds unless step t-1 or t-2 moved
             // this proposal's particle
-            const bool mv1 = t >= 1 && s_acc[(t - 1) & 3] != 0 && !nomove_prev && j_prev == g.j;
-            const bool mv2 = t >= 2 && s_acc[(t - 2) & 3] != 0 && !nomove_prev2 && j_prev2 == g.j;
+            const bool mv1 = t >= 1 && s_acc[(t - 1) & 7] != 0 && !nomove_prev && j_prev == g.j;
+            const bool mv2 = t >= 2 && s_acc[(t - 2) & 7] != 0 && !nomove_prev2 && j_prev2 == g.j;
             const bool dk_pre = pbc && t > 0 && !mv1 && !mv2;
             if (!idle) {
               if (dk_pre) {
@@ -922,12 +859,16 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
                   }
                 });
               }
+              if (!need_state()) {
+                fail = true;
+                break;
+              }
+              const double hk = (cb == 0 && k < C) ? __ldcg(&S.Hhat[k]) : 0.0;
               __syncwarp();
-              // the block of G dK needs no state; only the first column block
-              // reads H (which the accepts change), after the state wait
               const int cbeg = cb * csz, cend = min(C, cbeg + csz);
-              double gk = 0.0;
+              double contrib = 0.0;
               if (k < C) {
+                double gk = 0.0;
                 if (gpre && it == lw) {
 #pragma unroll
                   for (int i = 0; i < MC_GPRE; i++)
@@ -936,17 +877,6 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
                   for (int c = cbeg; c < cend; c++) gk += __ldcg(&S.G[(size_t)c * C + k]) * st[c];
                 }
                 S.gK[(size_t)(t & 3) * MC_NF_COLS * C + (size_t)cb * C + k] = gk;
-              }
-              double hk = 0.0;
-              if (cb == 0) {
-                if (!need_state()) {
-                  fail = true;
-                  break;
-                }
-                hk = k < C ? __ldcg(&S.Hhat[k]) : 0.0;
-              }
-              double contrib = 0.0;
-              if (k < C) {
                 const double Wk = is_square(k) ? 1.0 : 2.0;
                 contrib = Wk * st[k] * (0.5 * gk + hk);
               }
@@ -982,14 +912,7 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
                 c1 = e1;
                 c2 = e2;
               }
-              // the accept of step t-1 changed the lists of its two finest
-              // cells only (every earlier accept preceded the decision of
-              // step t-1); other cells need no wait
-              const bool touched = s_acc[(t - 1) & 3] != 0 && !nomove_prev &&
-                                   ((c0 == cf_prev[0] && c1 == cf_prev[1] && c2 == cf_prev[2]) ||
-                                    (c0 == cfn_prev[0] && c1 == cfn_prev[1] && c2 == cfn_prev[2]));
-              if ((t >= 2 && !counter_wait(S.bar, cum_at(s_cumB, t - 2), S.status, rp.wait_ns)) ||
-                  (t > 0 && touched && !need_state())) {
+              if (!need_state()) {
                 fail = true;
                 break;
               }
@@ -1137,8 +1060,7 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
             bool own[2] = {false, false};
             int lsm = 0;  // large level of the item (0: small level)
             if (a >= 0) {
-              if (!counter_wait(&dcnt[t & 3], cumD[t & 3], S.status, rp.wait_ns) || !sync_prev() ||
-                  !(a < S.nsmall ? need_small(t - 1) : need_large(t - 1))) {
+              if (!counter_wait(&dcnt[16 * (t & 3)], cumD[t & 3], S.status, rp.wait_ns) || !need_state()) {
                 fail = true;
                 break;
               }
@@ -1193,11 +1115,6 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
                 }
               }
             }
-            // bookkeeping and K/H: after those of the step before
-            if (a < 0 && !need_state()) {
-              fail = true;
-              break;
-            }
             if (!decided) {
               if (!flag_wait(&s_dstep, t, &s_abort, S.status, rp.wait_ns)) {
                 fail = true;
@@ -1208,11 +1125,11 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
                 break;
               }
               decided = true;
-              accepted = s_acc[gi] != 0;
+              accepted = s_acc[t & 7] != 0;
               if (prof_on && lane == 0) prof_item(rp.prof, 11, s_tpub[gi]);
             }
             if (!accepted) break;  // rejected: nothing to apply
-            const double dE_used = s_dEu[gi];
+            const double dE_used = s_dEu[t & 7];
             if (b == 0) {
               // ---- bookkeeping: energy, dipole, positions, cell lists
               const int nL = S.nL, cap = S.cap;
@@ -1295,9 +1212,7 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
               }
             }
             __syncwarp();
-            // arrival: bookkeeping and K/H, small-level cells and large-level
-            // targets on their own counters
-            if (lane == 0) red_release_add(a < 0 ? S.bar : &S.sync[a < S.nsmall ? 6 : 7], 1ull);
+            if (lane == 0) red_release_add(S.bar, 1ull);
             if (prof_on && lane == 0) {
               prof_item(rp.prof, ptype, t_item);
               prof_item(rp.prof, 13, s_tpub[gi]);
@@ -1313,11 +1228,6 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
       nomove_prev2 = nomove_prev;
       j_prev = g.j;
       nomove_prev = nomove;
-#pragma unroll
-      for (int d = 0; d < 3; d++) {
-        cf_prev[d] = g.cf[d];
-        cfn_prev[d] = g.cfn[d];
-      }
       if (lane == 0) flag_publish(&s_wdone[warp], t);
       __syncwarp();
     }

@@ -148,7 +148,7 @@ int launch_chain(mc_ctx* c, RunParams& rp) {
   if (async) {
     // counters, partial-slot ring at its "not written" pattern (all bits
     // set), the four small-level contribution buffers clear
-    CK(cudaMemsetAsync(c->h.sync, 0, sizeof(unsigned long long) * 16, c->stream));
+    CK(cudaMemsetAsync(c->h.sync, 0, sizeof(unsigned long long) * 128, c->stream));
     CK(cudaMemsetAsync(c->h.partials, 0xFF, sizeof(double) * 4 * MC_MAX_ITEMS, c->stream));
     if (c->h.nsmall > 0)
       CK(cudaMemsetAsync(c->h.dsmall, 0, sizeof(double) * 4 * (size_t)c->h.nsmall * c->h.C, c->stream));
@@ -481,7 +481,7 @@ int mc_init(mc_ctx** out, int64_t n, const double* pos, const double* q, double 
   DA(h.Hhat2, sizeof(double) * C);
   DA(h.dipv2, sizeof(double) * 3);
   DA(h.dsmall, sizeof(double) * 4 * (size_t)std::max(1, h.nsmall) * C);
-  DA(h.sync, sizeof(unsigned long long) * 16);
+  DA(h.sync, sizeof(unsigned long long) * 128);
   DA(h.dacc, sizeof(double) * 8 * (size_t)(levels - h.lmin + 1) * MC_DSLOTS * C);
   DA(h.dKpre, sizeof(double) * 4 * C);
   DCK(cudaMemsetAsync(h.dsmall, 0, sizeof(double) * 4 * (size_t)std::max(1, h.nsmall) * C, c->stream));

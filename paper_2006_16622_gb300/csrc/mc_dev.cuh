@@ -74,8 +74,8 @@ struct McSys {
   double* dsmall;    // [4 * nsmall * C] (rotating buffers: three or four)
   int ls_end;        // first level with more than 4 cells per axis (or L + 1)
   int nsmall;        // cells of levels lmin .. ls_end-1 (the first cells of Lhat)
-  unsigned long long* sync;  // [16]: [l] read epoch of level l, [12] near items done;
-                             // mc_async.cu: [0..3] contributions, [4] K item, [5] decisions
+  unsigned long long* sync;  // [128]: [l] read epoch of level l, [12] near items done;
+                             // mc_async.cu: counters at [16 i], i = 1..6
   // speculative accept: Alg. L.2 contributions staged during the proposal
   double* dacc;      // [4 (step) * (L - lmin + 1) * 2 * MC_DSLOTS * C] (phased: by step parity;
                      // mc_async.cu: by step mod 4 and side)
