@@ -980,8 +980,10 @@ int batch_enqueue(mc_batch* b) {
     CK(mc_launch_batch_pipe(b->d_systems, b->d_rps, b->d_cta_chain, b->d_cta_rank,
                             b->d_chain_ctas, b->prec, b->nCTA, b->stream));
   } else {
+    // phased FP64: the column-scaled contributions (fewer FP64 instructions
+    // for this throughput-bound form)
     const int var = b->ctxs[0]->h.method == 1 ? MC_VAR_MM
-                    : b->schedule == MC_SCHEDULE_PHASED ? MC_VAR_SPEC
+                    : b->schedule == MC_SCHEDULE_PHASED ? (b->prec == MC_FP64 ? MC_VAR_SPECW : MC_VAR_SPEC)
                                                        : MC_VAR_PLAIN;
     CK(mc_launch_batch(b->d_systems, b->d_rps, b->d_cta_chain, b->d_cta_rank, b->d_chain_ctas,
                        b->prec, var, b->nCTA, b->stream));

@@ -38,7 +38,12 @@
 template <typename TE, int kVar>
 __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunParams& rp,
                                            const int nCTA, const int cta) {
-  constexpr bool spec = kVar == MC_VAR_SPEC;
+  // MC_VAR_SPECW: the speculative contributions in the column-scaled form
+  // (5 flops per recurrence step, no in-register sum of the two sides: each
+  // side its own staged slot, P_n^m applied by the apply's multiply-add):
+  // fewer FP64 instructions, for the throughput-bound batched FP64 form
+  constexpr bool specw = kVar == MC_VAR_SPECW;
+  constexpr bool spec = kVar == MC_VAR_SPEC || specw;
   constexpr bool mm = kVar == MC_VAR_MM;
   __shared__ McSys S;
   __shared__ HarmTabs<TE> tabs;
@@ -52,9 +57,12 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
   // k * width of level l for k = -3..3 (k + 3), and in the evaluation type
   __shared__ double s_kw[MC_MAXLEV + 2][7];
   __shared__ TE s_kwe[MC_MAXLEV + 2][7];
+  __shared__ TE s_iW[specw ? MC_PMAX + 1 : 1][16];
+  __shared__ double s_P[specw ? (MC_PMAX + 1) * (MC_PMAX + 1) : 1];
 
   if (threadIdx.x == 0) S = *sysp;
   harm_tabs_init<TE>(&tabs);
+  if constexpr (specw) irregular_w_tabs<TE>(s_iW, s_P);
   il_table_init(il);
   __syncthreads();
   for (int i = threadIdx.x; i < (MC_MAXLEV + 2) * 7; i += blockDim.x) {
@@ -284,7 +292,9 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
     // (staged slots by step parity, small-level deltas in three rotating
     // buffers: the accept of the previous step may still read its own)
     const int nlev = L - S.lmin + 1;
-    auto dslot = [&](int l, int slot) -> double* {
+    auto dslot = [&](int l, int slot, int side) -> double* {
+      if constexpr (specw)
+        return S.dacc + ((((size_t)(t & 1) * nlev + (L - l)) * 2 + side) * MC_DSLOTS + slot) * C;
       return S.dacc + (((size_t)(t & 1) * nlev + (L - l)) * MC_DSLOTS + slot) * C;
     };
     const size_t nsC = (size_t)S.nsmall * C;
@@ -343,13 +353,17 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
             }
           }
           double* Dt = dsm + (size_t)(S.lev_off[l] + (se.t3[0] * nl + se.t3[1]) * nl + se.t3[2]) * C;
-          irregular_group_s<TE>(&tabs, p, dx, dy, dz, f, [&](int t2, int n, int m, bool v, TE vr, TE vi) {
+          auto add = [&](int t2, int n, int m, bool v, TE vr, TE vi) {
             if (se.valid && v) {
               const int kk = rl_re(n, m);
               atomicAdd(&Dt[kk], to_double(vr));
               if (m) atomicAdd(&Dt[kk + 1], to_double(neg_bits(vi)));
             }
-          });
+          };
+          if constexpr (specw)
+            irregular_group_w<TE>(&tabs, s_iW, p, dx, dy, dz, f, add);
+          else
+            irregular_group_s<TE>(&tabs, p, dx, dy, dz, f, add);
         } else {
           // targets 2k (groups 0, 1) and 2k+1 (groups 2, 3); group 0/2 the
           // alpha side, 1/3 the alpha' side
@@ -382,17 +396,29 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
               dz = from_double<TE>(s_off[side][l][2]) - s_kwe[l][ofs[2] + 3];
             }
           }
-          double* Ds = dslot(l, exists ? kt : 0);
-          irregular_group_s<TE>(&tabs, p, dx, dy, dz, f, [&](int t2, int n, int m, bool v, TE vr, TE vi) {
-            const TE cr = vr, ci = neg_bits(vi);
-            const TE orr = __shfl_xor_sync(0xffffffffu, cr, 8);
-            const TE oii = __shfl_xor_sync(0xffffffffu, ci, 8);
-            if (side == 0 && own && v) {
-              const int kk = rl_re(n, m);
-              __stcg(&Ds[kk], to_double(cr + orr));
-              if (m) __stcg(&Ds[kk + 1], to_double(ci + oii));
-            }
-          });
+          if constexpr (specw) {
+            // each side in its own slot, column-scaled
+            double* Ds = dslot(l, exists ? kt : 0, side);
+            irregular_group_w<TE>(&tabs, s_iW, p, dx, dy, dz, f, [&](int t2, int n, int m, bool v, TE vr, TE vi) {
+              if (own && v) {
+                const int kk = rl_re(n, m);
+                __stcg(&Ds[kk], to_double(vr));
+                if (m) __stcg(&Ds[kk + 1], to_double(neg_bits(vi)));
+              }
+            });
+          } else {
+            double* Ds = dslot(l, exists ? kt : 0, 0);
+            irregular_group_s<TE>(&tabs, p, dx, dy, dz, f, [&](int t2, int n, int m, bool v, TE vr, TE vi) {
+              const TE cr = vr, ci = neg_bits(vi);
+              const TE orr = __shfl_xor_sync(0xffffffffu, cr, 8);
+              const TE oii = __shfl_xor_sync(0xffffffffu, ci, 8);
+              if (side == 0 && own && v) {
+                const int kk = rl_re(n, m);
+                __stcg(&Ds[kk], to_double(cr + orr));
+                if (m) __stcg(&Ds[kk + 1], to_double(ci + oii));
+              }
+            });
+          }
         }
         if (prof_on && lane == 0) prof_item(rp.prof, nl <= 4 ? 7 : 8, t_item);
         continue;
@@ -792,7 +818,7 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
           for (int i = 0; i < 8; i++) {
             const int kk = lane + 32 * i;
             if (kk < C) {
-              __stcg(&Lt[kk], v[i] + w[i]);
+              __stcg(&Lt[kk], specw ? fma(s_P[specw ? kk : 0], w[i], v[i]) : v[i] + w[i]);
               __stcg(&Dt[kk], 0.0);
             }
           }
@@ -810,7 +836,8 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
         const int cn[3] = {g.cfn[0] >> sh, g.cfn[1] >> sh, g.cfn[2] >> sh};
         const LargeItem li = large_item(il, co, cn, nl, pbc, lev_items[l] == 189, b);
         if (li.owner) {
-          const double* Ds = dslot(l, b);
+          const double* Ds = dslot(l, b, 0);
+          const double* Ds1 = dslot(l, b, 1);
           double* Lt = S.Lhat + (size_t)(S.lev_off[l] + (li.tc[0] * nl + li.tc[1]) * nl + li.tc[2]) * C;
           double v[8], w[8];
 #pragma unroll
@@ -818,11 +845,12 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
             const int kk = lane + 32 * i;
             v[i] = kk < C ? __ldcg(&Lt[kk]) : 0.0;
             w[i] = kk < C ? __ldcg(&Ds[kk]) : 0.0;
+            if constexpr (specw) w[i] += kk < C ? __ldcg(&Ds1[kk]) : 0.0;
           }
 #pragma unroll
           for (int i = 0; i < 8; i++) {
             const int kk = lane + 32 * i;
-            if (kk < C) __stcg(&Lt[kk], v[i] + w[i]);
+            if (kk < C) __stcg(&Lt[kk], specw ? fma(s_P[specw ? kk : 0], w[i], v[i]) : v[i] + w[i]);
           }
         }
         if (prof_on && lane == 0) prof_item(rp.prof, 5, t_item);
@@ -1018,6 +1046,11 @@ cudaError_t mc_launch_batch(const McSys* const* d_systems, RunParams* d_rps, con
   cfg.numAttrs = 1;
   if (var == MC_VAR_MM)
     return batch_launch<MC_VAR_MM>(&cfg, prec, d_systems, d_rps, d_cta_chain, d_cta_rank, d_chain_ctas);
+  if (var == MC_VAR_SPECW && !prec)  // (FP64 only)
+    return cudaLaunchKernelEx(&cfg, mc_batch_kernel<double, MC_VAR_SPECW>, d_systems, d_rps, d_cta_chain,
+                              d_cta_rank, d_chain_ctas);
+  if (var == MC_VAR_SPECW)
+    return batch_launch<MC_VAR_SPEC>(&cfg, prec, d_systems, d_rps, d_cta_chain, d_cta_rank, d_chain_ctas);
   if (var == MC_VAR_SPEC)
     return batch_launch<MC_VAR_SPEC>(&cfg, prec, d_systems, d_rps, d_cta_chain, d_cta_rank,
                                      d_chain_ctas);
@@ -1030,12 +1063,13 @@ int mc_batch_max_ctas(int prec) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const void* fns[3][2] = {
+  const void* fns[4][2] = {
       {(const void*)mc_batch_kernel<double, MC_VAR_PLAIN>, (const void*)mc_batch_kernel<float, MC_VAR_PLAIN>},
       {(const void*)mc_batch_kernel<double, MC_VAR_SPEC>, (const void*)mc_batch_kernel<float, MC_VAR_SPEC>},
-      {(const void*)mc_batch_kernel<double, MC_VAR_MM>, (const void*)mc_batch_kernel<float, MC_VAR_MM>}};
+      {(const void*)mc_batch_kernel<double, MC_VAR_MM>, (const void*)mc_batch_kernel<float, MC_VAR_MM>},
+      {(const void*)mc_batch_kernel<double, MC_VAR_SPECW>, (const void*)mc_batch_kernel<float, MC_VAR_SPEC>}};
   int best = 1 << 30;
-  for (int v = 0; v < 3; v++) {
+  for (int v = 0; v < 4; v++) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fns[v][prec ? 1 : 0], MC_THREADS, 0) !=
         cudaSuccess)
       return 0;

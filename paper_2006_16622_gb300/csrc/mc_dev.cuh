@@ -38,6 +38,7 @@
 #define MC_VAR_PLAIN 0  // chain kernel variants (see chain_body)
 #define MC_VAR_SPEC 1
 #define MC_VAR_MM 2
+#define MC_VAR_SPECW 3  // MC_VAR_SPEC, column-scaled contributions (batched FP64)
 #define MC_DSLOTS 380   // staged accept contributions per level (>= 378 targets)
 
 // ---------------------------------------------------------------- state
