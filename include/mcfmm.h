@@ -173,6 +173,13 @@ int mc_lattice_sums(int lmax, double *out);
 #define MC_SCHEDULE_PLAIN 2
 #define MC_SCHEDULE_ASYNC 3
 int mc_set_schedule(mc_ctx *ctx, int schedule);
+/* CTAs of the persistent chain launches of ctx (mc_run, mc_propose,
+ * mc_accept): 1 <= n_cta <= the multiprocessor count, one CTA per SM; 0
+ * restores the default (every SM).  The work items of a step are dealt over
+ * the warps of the grid and their partial results are combined in one fixed
+ * order, so the results do not depend on n_cta.  MC_ERR_ARG outside that
+ * range; takes effect at the next launch. */
+int mc_set_ctas(mc_ctx *ctx, int n_cta);
 /* Status of the last asynchronous launch (MC_OK, MC_ERR_TIMEOUT, ...). */
 int mc_status(mc_ctx *ctx);
 /* Wait-limit of the device-side grid barrier in nanoseconds (default 2e9);

@@ -849,6 +849,12 @@ int mc_set_schedule(mc_ctx* c, int schedule) {
   return MC_OK;
 }
 
+int mc_set_ctas(mc_ctx* c, int n_cta) {
+  if (!c || n_cta < 0 || n_cta > c->sms) return MC_ERR_ARG;
+  c->nCTA = n_cta == 0 ? c->sms : n_cta;
+  return MC_OK;
+}
+
 int mc_status(mc_ctx* c) {
   if (!c) return MC_ERR_ARG;
   return sync_status(c);

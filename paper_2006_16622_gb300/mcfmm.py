@@ -27,7 +27,7 @@ EXPORTED = ["mc_init", "mc_setup", "mc_propose", "mc_accept", "mc_run", "mc_ener
             "mc_lattice_sums", "mc_status", "mc_set_wait_limit", "mc_profile", "mc_profile_read",
             "mc_destroy", "mc_strerror", "mc_p2l_level_noalloc", "mc_batch_create",
             "mc_batch_tune", "mc_batch_run", "mc_batch_info", "mc_batch_destroy",
-            "mc_set_schedule", "mc_batch_set_schedule", "mc_inject_wait_fault",
+            "mc_set_schedule", "mc_set_ctas", "mc_batch_set_schedule", "mc_inject_wait_fault",
             "mc_get_multipole", "mc_set_lj"]
 
 
@@ -81,6 +81,7 @@ def load(path: str = LIB_PATH):
     L.mc_batch_run.argtypes = [P, I64, P, D, D, P, P, P, P]
     L.mc_batch_info.argtypes = [P, P, P]
     L.mc_set_schedule.argtypes = [P, I]
+    L.mc_set_ctas.argtypes = [P, I]
     L.mc_batch_set_schedule.argtypes = [P, I]
     L.mc_batch_destroy.argtypes = [P]
     L.mc_batch_destroy.restype = None
@@ -228,6 +229,9 @@ class Context:
 
     def set_schedule(self, schedule):
         _check(load().mc_set_schedule(self._h, int(schedule)), "mc_set_schedule")
+
+    def set_ctas(self, n_cta):
+        _check(load().mc_set_ctas(self._h, int(n_cta)), "mc_set_ctas")
 
     def set_wait_limit(self, ns):
         _check(load().mc_set_wait_limit(self._h, int(ns)), "mc_set_wait_limit")
