@@ -219,6 +219,28 @@ def algorithmic_flops_per_step(p, levels, nbar, nu):
     return f_prop + nu * f_acc, f_prop, f_acc
 
 
+def setup_flops(n, p, levels, mode):
+    """FP64 flops of one setup pass from the algorithm (periodic box, levels
+    2..L).  Alg. L.3 ("p2l"): per charge, level and interaction-list cell one
+    irregular harmonic set and a C-length multiply-add.  Fast mode ("fmm"):
+    charge-to-multipole at the finest level, multipole-to-multipole up the
+    tree and multipole-to-local over every cell's 189 interaction-list cells,
+    each translation counted as a dense C x C operator (2 C^2).  Both add the
+    initial energy: per charge the L - 1 expansion evaluations and the
+    27-cell direct sum (11 flops a pair)."""
+    C = (p + 1) ** 2
+    hset = 3 * (p + 1) * (p + 2)
+    L_eff = levels - 1
+    nbar = n / (8 ** (levels - 1))
+    energy = n * (L_eff * (hset + 2 * C) + 27 * nbar * 11)
+    if mode == "p2l":
+        return n * L_eff * 189 * (hset + 2 * C) + energy
+    cells = [8 ** (l - 1) for l in range(2, levels + 1)]
+    m2l = sum(cells) * 189 * 2 * C * C
+    m2m = sum(cells[1:]) * 2 * C * C
+    return n * (hset + 2 * C) + m2m + m2l + energy
+
+
 def bytes_per_step(p, levels, nbar, nu):
     C = (p + 1) ** 2
     L_eff = levels - 1
@@ -321,6 +343,13 @@ def huge_workload_leg(args, stream, flush):
         out[f"setup_{name}_s"] = timed(lambda: ctx.setup(mode))
         energies[name] = ctx.energy()
     out["fmm_energy_rel_gap"] = abs(energies["fmm"] - energies["p2l"]) / abs(energies["p2l"])
+    out["setup_roofline"] = {}
+    for name in ("p2l", "fmm"):
+        f = setup_flops(len(q), W.p, W.levels, name)
+        ach = f / out[f"setup_{name}_s"]
+        out["setup_roofline"][name] = {"bound": "alu", "flops": f, "achieved": ach / 1e12,
+                                       "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+                                       "frac": ach / FP64_PEAK_FLOPS}
     ctx.close()
     for prec, name in ((mcfmm.FP64, "fp64"), (mcfmm.FP32_EVAL, "fp32_eval")):
         ctx = mcfmm.Context(pos, q, W.a, W.levels, W.p, precision=prec, stream=stream.cuda_stream)

@@ -175,7 +175,8 @@ int mc_lattice_sums(int lmax, double *out);
 int mc_set_schedule(mc_ctx *ctx, int schedule);
 /* CTAs of the persistent chain launches of ctx (mc_run, mc_propose,
  * mc_accept): 1 <= n_cta <= the multiprocessor count, one CTA per SM; 0
- * restores the default (every SM).  The work items of a step are dealt over
+ * restores the default: every SM, except 5/7 of them for the phased chain of
+ * an FP32-eval context (measured faster).  The work items of a step are dealt over
  * the warps of the grid and their partial results are combined in one fixed
  * order, so the results do not depend on n_cta.  MC_ERR_ARG outside that
  * range; takes effect at the next launch. */

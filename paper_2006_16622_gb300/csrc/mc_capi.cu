@@ -55,7 +55,7 @@ struct mc_ctx {
   McSys* d_sys;   // device copy
   cudaStream_t stream;
   int dev;
-  int nCTA;
+  int nCTA;  // chain grid set by mc_set_ctas; 0: the default by form and schedule
   int sms;
   int setup_done;
   long long steps_total;
@@ -143,6 +143,15 @@ int launch_chain(mc_ctx* c, RunParams& rp) {
   rp.nf_cols = piped ? 4 : MC_NF_COLS;
   rp.spec = (!mm && (c->schedule == MC_SCHEDULE_PHASED || c->schedule == MC_SCHEDULE_ASYNC)) ? 1 : 0;
   rp.chain = 0u;
+  // grid: the caller's (mc_set_ctas), else every SM, except for the phased
+  // FP32-eval chain of the local method, which is faster on 5/7 of the SMs
+  // (GB300, 108 of 152 CTAs: +0.5..4 % at N = 1e4..1e6, its short items pay
+  // more for the barrier arrivals than they gain from the extra warps); the
+  // barrier-free chain needs every SM (its step's items fill the grid's
+  // warps: -4 % on 128 CTAs, -15 % on 114 at N = 1e5)
+  int grid = c->nCTA;
+  if (grid == 0)
+    grid = (!mm && !async && !piped && rp.spec && c->h.prec == MC_FP32_EVAL) ? (5 * c->sms) / 7 : c->sms;
   CK(cudaMemsetAsync(c->h.bar, 0, sizeof(unsigned long long), c->stream));
   CK(cudaMemsetAsync(c->h.status, 0, sizeof(int), c->stream));
   if (async) {
@@ -152,18 +161,18 @@ int launch_chain(mc_ctx* c, RunParams& rp) {
     CK(cudaMemsetAsync(c->h.partials, 0xFF, sizeof(double) * 4 * MC_MAX_ITEMS, c->stream));
     if (c->h.nsmall > 0)
       CK(cudaMemsetAsync(c->h.dsmall, 0, sizeof(double) * 4 * (size_t)c->h.nsmall * c->h.C, c->stream));
-    CK(mc_launch_async(c->d_sys, rp, c->h.prec, c->nCTA, c->stream));
+    CK(mc_launch_async(c->d_sys, rp, c->h.prec, grid, c->stream));
   } else if (piped) {
     // accept of step k overlaps the proposal of k+1
     CK(cudaMemsetAsync(c->h.sync, 0, sizeof(unsigned long long) * 16, c->stream));
     CK(cudaMemsetAsync(c->h.dsmall, 0, sizeof(double) * 3 * (size_t)c->h.nsmall * c->h.C, c->stream));
-    CK(mc_launch_pipe(c->d_sys, rp, c->h.prec, c->nCTA, c->stream));
+    CK(mc_launch_pipe(c->d_sys, rp, c->h.prec, grid, c->stream));
   } else {
     // the two small-level delta buffers of the speculative accept start clear
     if (rp.spec && c->h.nsmall > 0)
       CK(cudaMemsetAsync(c->h.dsmall, 0, sizeof(double) * 3 * (size_t)c->h.nsmall * c->h.C, c->stream));
     CK(mc_launch_chain(c->d_sys, rp, c->h.prec,
-                       mm ? MC_VAR_MM : (rp.spec ? MC_VAR_SPEC : MC_VAR_PLAIN), c->nCTA, c->stream));
+                       mm ? MC_VAR_MM : (rp.spec ? MC_VAR_SPEC : MC_VAR_PLAIN), grid, c->stream));
   }
   return MC_OK;
 }
@@ -516,8 +525,7 @@ int mc_init(mc_ctx** out, int64_t n, const double* pos, const double* q, double 
     k_far_operator<<<grid_for(c->sms, (size_t)C * C, 256), 256, 0, c->stream>>>(p, box, d_st, h.G);
     DCK(cudaGetLastError());
   }
-  c->nCTA = mc_chain_max_ctas(precision);
-  if (c->nCTA < 1) {
+  if (mc_chain_max_ctas(precision) < 1) {
     mc_destroy(c);
     return MC_ERR_CUDA;
   }
@@ -851,7 +859,7 @@ int mc_set_schedule(mc_ctx* c, int schedule) {
 
 int mc_set_ctas(mc_ctx* c, int n_cta) {
   if (!c || n_cta < 0 || n_cta > c->sms) return MC_ERR_ARG;
-  c->nCTA = n_cta == 0 ? c->sms : n_cta;
+  c->nCTA = n_cta;
   return MC_OK;
 }
 
