@@ -974,7 +974,7 @@ double orc_propose(orc_sys *s, int64_t j, const double rnew[3]) {
           }
         }
   }
-  /* self-interaction removal: line 8 of Alg. 1, replaced with periodic
+  /* self-interaction removal of Alg. 1, replaced with periodic
    * boundaries by the sum over the 27 images plus the constant for the 26
    * image copies counted on the old side */
   if (s->bc == ORC_BC_PBC) {

@@ -386,6 +386,19 @@ def test_proposal_stream_statistics():
     assert not np.array_equal(a, b) and not np.array_equal(a, c)
 
 
+def test_philox_known_answers():
+    """The proposal stream's generator is Philox4x32-10 (Salmon et al.,
+    SC'11): the oracle's implementation reproduces the published
+    known-answer values (tests/golden/philox_kat.txt)."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox_kat.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        w = [int(x, 16) for x in r]
+        out = O.philox(w[0:4], w[4:6])
+        assert [int(v) for v in out] == w[6:10], r
+
+
 def test_fmm_variant_setup_converges_to_exact_setup_and_direct_sums():
     """The FMM-variant setup (Sec. 3.2: per-level multipoles translated into
     each cell's interaction list) equals Alg. L.3 up to the multipole
