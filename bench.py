@@ -29,6 +29,17 @@ sys.path.insert(0, ROOT)
 METRIC = "MH steps/sec at N=1e5, p=12: plain FP64 vs FP32-eval/FP64-acc and batched"
 UNIT = "MH steps/s"
 FP64_PEAK_FLOPS = 152 * 4 * 2.070e9  # 152 SMs x 4 FP64 flop/clk/SM (2 FMA lanes) x max clock
+FP32_PEAK_FLOPS = 152 * 256 * 2.070e9  # 152 SMs x 128 FP32 lanes x 2 flop (FMA) x max clock
+
+
+def hbm_peak_bytes():
+    """Measured copy bandwidth of this GPU model (MEASURED_PEAKS.json), else
+    6.8 TB/s (an earlier GB300 measurement)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]) * 1e9, "measured"
+    except (OSError, ValueError, KeyError):
+        return 6.8e12, "fallback"
 
 
 def parse():
@@ -165,7 +176,10 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # raw samples: $MC_CLOCKS_DIR if set, else the system's temporary folder
+        import tempfile
+        out_dir = os.environ.get("MC_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"clocks_rank{gpu_index}.csv")
 
     def start(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
@@ -241,6 +255,24 @@ def setup_flops(n, p, levels, mode):
     return n * (hset + 2 * C) + m2m + m2l + energy
 
 
+def roofline_step_time(p, levels, nbar, nu, fp32_eval):
+    """Speed-of-light time of one MH step: the slowest of the evaluation
+    flops at their unit's peak, the FP64 flops at the FP64 peak and the bytes
+    at HBM bandwidth.  In the FP32-eval form the FP64 part is what stays
+    FP64: the far-lattice change (two harmonic sets about the box centre and
+    the dense operator), the image correction, the decision and, per accept,
+    the accumulator adds and the K/H update; everything else runs in FP32."""
+    C = (p + 1) ** 2
+    hset = 3 * (p + 1) * (p + 2)
+    F, _, _ = algorithmic_flops_per_step(p, levels, nbar, nu)
+    bw, _ = hbm_peak_bytes()
+    t_mem = bytes_per_step(p, levels, nbar, nu) / bw
+    if not fp32_eval:
+        return max(F / FP64_PEAK_FLOPS, t_mem)
+    f64 = 2 * hset + 2 * C * C + 4 * C + 27 * 11 + nu * (189 * (levels - 1) * C + 4 * C)
+    return max((F - f64) / FP32_PEAK_FLOPS, f64 / FP64_PEAK_FLOPS, t_mem)
+
+
 def bytes_per_step(p, levels, nbar, nu):
     C = (p + 1) ** 2
     L_eff = levels - 1
@@ -311,7 +343,7 @@ def batched_form(args, precision, stream, flush):
         c.close()
     return dict(value=len(ctxs) * Sb * args.steps / sum(durs), setup_s=setup_s, tune_s=tune_s,
                 ctas=[int(x) for x in ctas], nf_cols=nf, acceptance=acc,
-                sizes=[n for n, _, _, _ in systems])
+                sizes=[n for n, _, _, _ in systems], levels=[L for _, _, L, _ in systems])
 
 
 def huge_workload_leg(args, stream, flush):
@@ -648,6 +680,19 @@ def gpu_arm(args):
             "acceptance": rb32["acceptance"]}
     else:
         forms["batched_fp32_eval"] = None
+    # every form as a fraction of its roofline (rate x speed-of-light step time)
+    bw, bw_src = hbm_peak_bytes()
+    fr = {"fp64": value * roofline_step_time(W.p, W.levels, nbar, r64["nu"], False)}
+    if r32:
+        fr["fp32_eval"] = forms["fp32_eval"] * roofline_step_time(W.p, W.levels, nbar, r32["nu"], True)
+    if rb32:
+        for key, rb, f32 in (("batched_fp32_eval", rb32, True), ("batched_fp64", rb64, False)):
+            ts = [roofline_step_time(10, L, n / 8 ** (L - 1), rb["acceptance"], f32)
+                  for n, L in zip(rb["sizes"], rb["levels"])]
+            fr[key] = forms[key] * statistics.mean(ts)
+    fr["peaks"] = (f"FP64 {FP64_PEAK_FLOPS / 1e12:.2f} and FP32 {FP32_PEAK_FLOPS / 1e12:.1f} TFLOP/s derived "
+                   f"(unit counts x 2070 MHz), HBM {bw / 1e9:.0f} GB/s {bw_src}")
+    forms["roofline_frac"] = fr
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * r64["total"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
