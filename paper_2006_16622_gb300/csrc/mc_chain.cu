@@ -59,6 +59,14 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
   __shared__ TE s_kwe[MC_MAXLEV + 2][7];
   __shared__ TE s_iW[specw ? MC_PMAX + 1 : 1][16];
   __shared__ double s_P[specw ? (MC_PMAX + 1) * (MC_PMAX + 1) : 1];
+  // the contributions in pair-of-floats arithmetic (FP64 form): W, A_k and
+  // P_n^m as pairs, n of every real-layout index, and per level the
+  // power-of-two unit k_l (2^k_l <= cell width < 2^(k_l + 1))
+  __shared__ f2 s_W2[specw ? MC_PMAX + 1 : 1][16];
+  __shared__ f2 s_A2[16];
+  __shared__ f2 s_P2[specw ? (MC_PMAX + 1) * (MC_PMAX + 1) : 1];
+  __shared__ unsigned char s_nn[specw ? (MC_PMAX + 1) * (MC_PMAX + 1) : 1];
+  __shared__ int s_kl[MC_MAXLEV + 2];
 
   if (threadIdx.x == 0) S = *sysp;
   harm_tabs_init<TE>(&tabs);
@@ -70,6 +78,23 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
     const double v = (l >= 1 && l <= S.L) ? k * S.lev_w[l] : 0.0;
     s_kw[l][k + 3] = v;
     s_kwe[l][k + 3] = (TE)v;
+  }
+  if constexpr (specw) {
+    for (int k = threadIdx.x; k < (MC_PMAX + 1) * 16; k += blockDim.x)
+      s_W2[k / 16][k % 16] = f2_of((double)s_iW[k / 16][k % 16]);
+    for (int k = threadIdx.x; k < (MC_PMAX + 1) * (MC_PMAX + 1); k += blockDim.x) {
+      s_P2[k] = f2_of(s_P[k]);
+      int n = 0;
+      while ((n + 1) * (n + 1) <= k) n++;
+      s_nn[k] = (unsigned char)n;
+    }
+    if (threadIdx.x < 16) s_A2[threadIdx.x] = f2_of(threadIdx.x ? 2.0 * threadIdx.x - 1.0 : 0.0);
+    if (threadIdx.x < MC_MAXLEV + 2) {
+      const int l = threadIdx.x;
+      s_kl[l] = (l >= 1 && l <= S.L)
+                    ? (int)((__double_as_longlong(S.lev_w[l]) >> 52) & 0x7ff) - 1023
+                    : 0;
+    }
   }
   __syncthreads();
 
@@ -360,10 +385,24 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
               if (m) atomicAdd(&Dt[kk + 1], to_double(neg_bits(vi)));
             }
           };
-          if constexpr (specw)
+          if constexpr (specw && sizeof(TE) == 8) {
+            // pair-of-floats recurrence in units of 2^k_l, back to the
+            // true scale (2^(-k_l (n + 1))) for the atomic adds
+            const int kl = s_kl[l];
+            irregular_group_w2(s_A2, s_W2, p, f2_from_double((double)dx, -kl), f2_from_double((double)dy, -kl),
+                               f2_from_double((double)dz, -kl), f2_from_double((double)f, 0),
+                               [&](int t2, int n, int m, bool v, f2 vr, f2 vi) {
+                                 if (se.valid && v) {
+                                   const int kk = rl_re(n, m), e = -kl * (n + 1);
+                                   atomicAdd(&Dt[kk], f2_to_double(vr, e));
+                                   if (m) atomicAdd(&Dt[kk + 1], f2_to_double(f2_neg(vi), e));
+                                 }
+                               });
+          } else if constexpr (specw) {
             irregular_group_w<TE>(&tabs, s_iW, p, dx, dy, dz, f, add);
-          else
+          } else {
             irregular_group_s<TE>(&tabs, p, dx, dy, dz, f, add);
+          }
         } else {
           // targets 2k (groups 0, 1) and 2k+1 (groups 2, 3); group 0/2 the
           // alpha side, 1/3 the alpha' side
@@ -396,8 +435,21 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
               dz = from_double<TE>(s_off[side][l][2]) - s_kwe[l][ofs[2] + 3];
             }
           }
-          if constexpr (specw) {
-            // each side in its own slot, column-scaled
+          if constexpr (specw && sizeof(TE) == 8) {
+            // each side in its own slot, column-scaled, as the pair (hi, lo)
+            // of the value in units of 2^k_l (the apply rescales)
+            double* Ds = dslot(l, exists ? kt : 0, side);
+            const int kl = s_kl[l];
+            irregular_group_w2(s_A2, s_W2, p, f2_from_double((double)dx, -kl), f2_from_double((double)dy, -kl),
+                               f2_from_double((double)dz, -kl), f2_from_double((double)f, 0),
+                               [&](int t2, int n, int m, bool v, f2 vr, f2 vi) {
+                                 if (own && v) {
+                                   const int kk = rl_re(n, m);
+                                   __stcg(reinterpret_cast<float2*>(&Ds[kk]), make_float2(vr.h, vr.l));
+                                   if (m) __stcg(reinterpret_cast<float2*>(&Ds[kk + 1]), make_float2(-vi.h, -vi.l));
+                                 }
+                               });
+          } else if constexpr (specw) {
             double* Ds = dslot(l, exists ? kt : 0, side);
             irregular_group_w<TE>(&tabs, s_iW, p, dx, dy, dz, f, [&](int t2, int n, int m, bool v, TE vr, TE vi) {
               if (own && v) {
@@ -839,18 +891,41 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
           const double* Ds = dslot(l, b, 0);
           const double* Ds1 = dslot(l, b, 1);
           double* Lt = S.Lhat + (size_t)(S.lev_off[l] + (li.tc[0] * nl + li.tc[1]) * nl + li.tc[2]) * C;
-          double v[8], w[8];
+          if constexpr (specw && sizeof(TE) == 8) {
+            // L += P_n^m (w + w') 2^(-k_l (n + 1)): the two sides' pairs
+            // summed and scaled in pair arithmetic, one FP64 add into L
+            const int kl = s_kl[l];
+            double v[8];
+            float2 w0[8], w1[8];
 #pragma unroll
-          for (int i = 0; i < 8; i++) {
-            const int kk = lane + 32 * i;
-            v[i] = kk < C ? __ldcg(&Lt[kk]) : 0.0;
-            w[i] = kk < C ? __ldcg(&Ds[kk]) : 0.0;
-            if constexpr (specw) w[i] += kk < C ? __ldcg(&Ds1[kk]) : 0.0;
-          }
+            for (int i = 0; i < 8; i++) {
+              const int kk = lane + 32 * i;
+              v[i] = kk < C ? __ldcg(&Lt[kk]) : 0.0;
+              w0[i] = kk < C ? __ldcg(reinterpret_cast<const float2*>(&Ds[kk])) : make_float2(0.0f, 0.0f);
+              w1[i] = kk < C ? __ldcg(reinterpret_cast<const float2*>(&Ds1[kk])) : make_float2(0.0f, 0.0f);
+            }
 #pragma unroll
-          for (int i = 0; i < 8; i++) {
-            const int kk = lane + 32 * i;
-            if (kk < C) __stcg(&Lt[kk], specw ? fma(s_P[specw ? kk : 0], w[i], v[i]) : v[i] + w[i]);
+            for (int i = 0; i < 8; i++) {
+              const int kk = lane + 32 * i;
+              if (kk < C) {
+                const f2 t = f2_mul(s_P2[kk], f2_add({w0[i].x, w0[i].y}, {w1[i].x, w1[i].y}));
+                __stcg(&Lt[kk], v[i] + f2_to_double(t, -kl * (s_nn[kk] + 1)));
+              }
+            }
+          } else {
+            double v[8], w[8];
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+              const int kk = lane + 32 * i;
+              v[i] = kk < C ? __ldcg(&Lt[kk]) : 0.0;
+              w[i] = kk < C ? __ldcg(&Ds[kk]) : 0.0;
+              if constexpr (specw) w[i] += kk < C ? __ldcg(&Ds1[kk]) : 0.0;
+            }
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+              const int kk = lane + 32 * i;
+              if (kk < C) __stcg(&Lt[kk], specw ? fma(s_P[specw ? kk : 0], w[i], v[i]) : v[i] + w[i]);
+            }
           }
         }
         if (prof_on && lane == 0) prof_item(rp.prof, 5, t_item);
