@@ -79,23 +79,7 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
     s_kw[l][k + 3] = v;
     s_kwe[l][k + 3] = (TE)v;
   }
-  if constexpr (specw) {
-    for (int k = threadIdx.x; k < (MC_PMAX + 1) * 16; k += blockDim.x)
-      s_W2[k / 16][k % 16] = f2_of((double)s_iW[k / 16][k % 16]);
-    for (int k = threadIdx.x; k < (MC_PMAX + 1) * (MC_PMAX + 1); k += blockDim.x) {
-      s_P2[k] = f2_of(s_P[k]);
-      int n = 0;
-      while ((n + 1) * (n + 1) <= k) n++;
-      s_nn[k] = (unsigned char)n;
-    }
-    if (threadIdx.x < 16) s_A2[threadIdx.x] = f2_of(threadIdx.x ? 2.0 * threadIdx.x - 1.0 : 0.0);
-    if (threadIdx.x < MC_MAXLEV + 2) {
-      const int l = threadIdx.x;
-      s_kl[l] = (l >= 1 && l <= S.L)
-                    ? (int)((__double_as_longlong(S.lev_w[l]) >> 52) & 0x7ff) - 1023
-                    : 0;
-    }
-  }
+  if constexpr (specw) pair_w_tabs<TE>(s_iW, s_P, s_W2, s_A2, s_P2, s_nn, s_kl, S.lev_w, S.L);
   __syncthreads();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -597,9 +597,28 @@ __device__ __forceinline__ void irregular_group_w2(const f2* A2, const f2 (*W2)[
   }
 }
 
-// the pair-of-floats copies of the diagonal factors A_k of the irregular
-// tables and of the W table (irregular_group_w2), and P_n^m as pairs
 __device__ __forceinline__ f2 f2_of(double v) { return f2_from_double(v, 0); }
+
+// Tables of irregular_group_w2 and of the apply that takes its pairs (read
+// after irregular_w_tabs has filled W and P): W and P_n^m as pairs, the
+// diagonal factors A_k = 2k - 1, n of every real-layout index, and per level
+// l the unit exponent k_l with 2^k_l <= lev_w[l] < 2^(k_l + 1).
+template <typename T>
+__device__ void pair_w_tabs(const T (*W)[16], const double* P, f2 (*W2)[16], f2* A2, f2* P2,
+                            unsigned char* nn, int* kl, const double* lev_w, int L) {
+  for (int k = threadIdx.x; k < (MC_PMAX + 1) * 16; k += blockDim.x) W2[k / 16][k % 16] = f2_of((double)W[k / 16][k % 16]);
+  for (int k = threadIdx.x; k < (MC_PMAX + 1) * (MC_PMAX + 1); k += blockDim.x) {
+    P2[k] = f2_of(P[k]);
+    int n = 0;
+    while ((n + 1) * (n + 1) <= k) n++;
+    nn[k] = (unsigned char)n;
+  }
+  if (threadIdx.x < 16) A2[threadIdx.x] = f2_of(threadIdx.x ? 2.0 * threadIdx.x - 1.0 : 0.0);
+  if (threadIdx.x < MC_MAXLEV + 2) {
+    const int l = threadIdx.x;
+    kl[l] = (l >= 1 && l <= L) ? (int)((__double_as_longlong(lev_w[l]) >> 52) & 0x7ff) - 1023 : 0;
+  }
+}
 
 template <typename T>
 __device__ void irregular_w_tabs(T (*W)[16], double* P) {
