@@ -120,6 +120,43 @@ def start_oracle(sample, warm=100):
     return p, q
 
 
+def _batch_oracle_worker(task):
+    """One chain of the batched workload in a spawned process: oracle setup
+    (untimed), 50 warm-up and `proposals` timed proposals on one core."""
+    n, a, L, i, proposals = task
+    import oracle
+    from paper_2006_16622_gb300.workloads import uniform_system
+    pos, q = uniform_system(n, a, seed=1000 + i)
+    s = oracle.System(pos, q, a, L, 10)
+    s.setup()
+    s.run(50, seed=i, step0=0, chain=i, beta=1.0, half_width=0.3, log=False)
+    t0 = time.perf_counter()
+    s.run(proposals, seed=i, step0=50, chain=i, beta=1.0, half_width=0.3, log=False)
+    return n, proposals / (time.perf_counter() - t0)
+
+
+def batched_cpu_baseline(proposals=300):
+    """The oracle on the batched workload (64 chains, N log-uniform in
+    [1000, 50000], p = 10), one process per host core: a sample of k chains
+    spread over the batch (k = cores, at most 16), each timed on its own
+    core while the others run.  The 64-chain batch with equal proposals per
+    chain then runs at k / sum_i(1 / rate_i) proposals/s on one core and k
+    times that on k cores (independent chains, balanced over the cores)."""
+    import multiprocessing as mp
+
+    from paper_2006_16622_gb300.workloads import batched_systems
+    systems = batched_systems(64, 1000, 50000, 0.1, 20.0)
+    k = max(1, min(os.cpu_count() or 1, 16))
+    pick = [systems[(j * len(systems)) // k] for j in range(k)]
+    with mp.get_context("spawn").Pool(processes=k) as pool:
+        res = pool.map(_batch_oracle_worker, [(n, a, L, i, proposals) for n, a, L, i in pick])
+    single = k / sum(1.0 / r for _, r in res)
+    return {"value": k * single, "unit": UNIT, "cores": k, "single_core": single, "kind": "oracle",
+            "sample": (f"{k} of the 64 chains (N {min(n for n, _ in res)}..{max(n for n, _ in res)}), "
+                       f"one process per core, {proposals} timed proposals each after 50 warm-up; "
+                       f"setups not timed; value = k cores x the single-core rate of the batch")}
+
+
 def cpu_baseline_from(res):
     return {"value": res["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": (f"{res['sample']} proposals (after 100 warm-up) of the same chain on the "
@@ -657,6 +694,13 @@ def gpu_arm(args):
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"oracle leg failed: {ex!r}"}
         proc.join(timeout=10)
+    cpu_batched = None
+    if world == 1 and not args.no_cpu and not args.no_batch:
+        try:
+            cpu_batched = batched_cpu_baseline()
+        except Exception as ex:  # noqa: BLE001
+            cpu_batched = {"value": None, "unit": UNIT, "kind": "oracle",
+                           "sample": f"batched oracle leg failed: {ex!r}"}
     forms = {"fp64": value}
     if r32:
         forms["fp64_phased_schedule"] = whole_job_rate(S * args.steps, world, r64p["total"])
@@ -702,7 +746,7 @@ def gpu_arm(args):
                        "fp32_eval_schedule": "phased (speculative accept contributions)",
                        "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"replicas x{world}"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roof, "cpu_baseline": cpu, "cpu_baseline_batched": cpu_batched, "e2e": e2e,
             "gpu_launches": args.steps, "clocks": r64["clocks"], "forms": forms,
             "precision_form": prec_stats,
             "setup_s": r64["setup_s"], "huge": huge, "size_sweep": sweep, "nacl_full_mc": nacl}
