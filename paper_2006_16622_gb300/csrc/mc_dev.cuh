@@ -528,7 +528,7 @@ __device__ __forceinline__ void irregular_group_w(const HarmTabs<T>* t, const T 
 }
 
 // irregular_group_w in pair-of-floats arithmetic (mc_df64.cuh, FP32 pipe,
-// ~48 significant bits): the displacement comes in units of 2^k, so value
+// ~46 significant bits): the displacement comes in units of 2^k, so value
 // (n, m) comes out multiplied by 2^(k (n + 1)) (the harmonics are
 // homogeneous of degree -(n + 1)); with |x| near 1 every value and its low
 // part stay inside the normal float range.  A2[k] = A_k, the diagonal

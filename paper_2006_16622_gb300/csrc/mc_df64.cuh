@@ -1,5 +1,6 @@
 // Pair-of-floats arithmetic ("double-float"): a value is the unevaluated sum
-// hi + lo of two floats with |lo| <= ulp(hi) / 2, about 48 significant bits.
+// hi + lo of two floats with |lo| <= ulp(hi) / 2; the pair holds 48
+// significant bits and each operation below is within ~2^-46 relative.
 // Built from the error-free transformations: Knuth's two-sum (exact sum of
 // two floats as a pair), the fast two-sum for |a| >= |b| (Dekker 1971) and
 // the exact product by one fused multiply-add.
