@@ -151,7 +151,7 @@ int launch_chain(mc_ctx* c, RunParams& rp) {
   // warps: -4 % on 128 CTAs, -15 % on 114 at N = 1e5)
   int grid = c->nCTA;
   if (grid == 0)
-    grid = (!mm && !async && !piped && rp.spec && c->h.prec == MC_FP32_EVAL) ? (5 * c->sms) / 7 : c->sms;
+    grid = (!mm && !async && !piped && rp.spec && c->h.prec == MC_FP32_EVAL) ? std::max(1, (5 * c->sms) / 7) : c->sms;
   CK(cudaMemsetAsync(c->h.bar, 0, sizeof(unsigned long long), c->stream));
   CK(cudaMemsetAsync(c->h.status, 0, sizeof(int), c->stream));
   if (async) {
