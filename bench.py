@@ -747,6 +747,11 @@ def gpu_arm(args):
                        "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "cpu_baseline_batched": cpu_batched, "e2e": e2e,
+            "paper_context": {"value": 1000.0, "unit": UNIT, "hardware": "1 core of an Intel Xeon E5-2650v2",
+                              "workload": "NaCl-like, N ~ 1e5, 12 expansion terms (p = 11), L = 4, periodic, "
+                                          "with Lennard-Jones",
+                              "note": "the paper's 'around 1 ms' per MH step with up to 1e5 charges (Sec. 2; "
+                                      "setting of Sec. 5.3): context only, another machine and workload"},
             "gpu_launches": args.steps, "clocks": r64["clocks"], "forms": forms,
             "precision_form": prec_stats,
             "setup_s": r64["setup_s"], "huge": huge, "size_sweep": sweep, "nacl_full_mc": nacl}
