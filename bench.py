@@ -750,7 +750,7 @@ def gpu_arm(args):
             "paper_context": {"value": 1000.0, "unit": UNIT, "hardware": "1 core of an Intel Xeon E5-2650v2",
                               "workload": "NaCl-like, N ~ 1e5, 12 expansion terms (p = 11), L = 4, periodic, "
                                           "with Lennard-Jones",
-                              "note": "the paper's 'around 1 ms' per MH step with up to 1e5 charges (Sec. 2; "
+                              "note": "the paper's cost of about 1 ms per MH step with up to 1e5 charges (Sec. 2; "
                                       "setting of Sec. 5.3): context only, another machine and workload"},
             "gpu_launches": args.steps, "clocks": r64["clocks"], "forms": forms,
             "precision_form": prec_stats,
