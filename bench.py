@@ -721,7 +721,9 @@ def gpu_arm(args):
             "proposals_per_chain_per_step": args.batch_steps, "ctas_per_chain": rb32["ctas"],
             "nf_cols": rb32["nf_cols"], "ctas_per_chain_fp64": rb64["ctas"],
             "nf_cols_fp64": rb64["nf_cols"], "setup_s": rb32["setup_s"], "tune_s": rb32["tune_s"],
-            "acceptance": rb32["acceptance"]}
+            "acceptance": rb32["acceptance"],
+            "fp64_arithmetic": "FP64, except the speculative contributions' irregular recurrence in "
+                               "pair-of-floats arithmetic (~46 bits) on the FP32 pipe; FP64 accumulators"}
     else:
         forms["batched_fp32_eval"] = None
     # every form as a fraction of its roofline (rate x speed-of-light step time)
