@@ -681,7 +681,7 @@ def gpu_arm(args):
             "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_FLOPS,
             "traffic": traffic_launch,
             "kernel": "mc_async_kernel<double>",
-            "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (recipe unit counts)",
+            "peak_source": "derived from unit counts: 152 SMs x 4 FP64 flop/clk x 2070 MHz",
             "flops_per_mh_step": F, "bytes_per_mh_step": bytes_per_step(W.p, W.levels, nbar, r64["nu"]),
             "acceptance": r64["nu"]}
     cpu = None
