@@ -87,3 +87,161 @@ def test_pair_arithmetic_error_bounds(tmp_path):
     assert e_mul <= bound and e_ms <= bound and e_add <= bound, (e_mul, e_ms, e_add)
     assert e_rs <= bound, e_rs
     assert out[6] == "1"
+
+
+GROUP_HARNESS = r"""
+#include <cmath>
+#include <complex>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <random>
+#include <thread>
+#include <vector>
+#define __device__
+#define __forceinline__ inline
+static inline long long __double_as_longlong(double x) { long long r; std::memcpy(&r, &x, 8); return r; }
+static inline double __longlong_as_double(long long x) { double r; std::memcpy(&r, &x, 8); return r; }
+static inline float __int_as_float(int x) { float r; std::memcpy(&r, &x, 4); return r; }
+static inline int __float_as_int(float x) { int r; std::memcpy(&r, &x, 4); return r; }
+static inline int __clz(unsigned x) { return x ? __builtin_clz(x) : 32; }
+static inline float rsqrtf(float x) { return 1.0f / std::sqrt(x); }
+
+// eight host threads stand for the eight lanes of one group; a shuffle is a
+// barrier, a store of each lane's value and a read of the source lane's
+struct Barrier {
+  std::mutex mu;
+  std::condition_variable cv;
+  int count = 0, gen = 0;
+  void wait() {
+    std::unique_lock<std::mutex> lk(mu);
+    const int g = gen;
+    if (++count == 8) { count = 0; gen++; cv.notify_all(); }
+    else cv.wait(lk, [&] { return gen != g; });
+  }
+};
+static Barrier g_bar;
+static float g_slot[8];
+thread_local unsigned t_lane;
+struct Dim { unsigned x; };
+#define threadIdx (Dim{t_lane})
+static float emu_exchange(float v, int src) {
+  g_bar.wait();
+  g_slot[t_lane] = v;
+  g_bar.wait();
+  return g_slot[src];
+}
+static float __shfl_up_sync(unsigned, float v, int d, int) {
+  const int l = (int)(t_lane & 7);
+  return emu_exchange(v, l >= d ? l - d : l);
+}
+static float __shfl_sync(unsigned, float v, int s, int) { return emu_exchange(v, s & 7); }
+#include "HEADER"
+
+typedef long double LD;
+typedef std::complex<LD> CX;
+
+int main() {
+  f2 A2[16], W2[16][16];
+  for (int k = 0; k < 16; k++) A2[k] = f2_from_double(k ? 2.0 * k - 1.0 : 0.0, 0);
+  for (int n = 0; n < 16; n++)
+    for (int m = 0; m < 16; m++)
+      W2[n][m] = f2_from_double(n >= m + 2 ? ((double)(n - 1) * (n - 1) - (double)m * m) /
+                                                 ((2.0 * n - 1.0) * (2.0 * n - 3.0)) : 0.0, 0);
+  std::mt19937_64 rng(11);
+  std::uniform_real_distribution<double> U(-1.0, 1.0);
+  double worst = 0.0;
+  int bad_cover = 0;
+  const int ps[4] = {6, 10, 12, 15};
+  for (int c = 0; c < 48; c++) {
+    const int p = ps[c % 4];
+    const int k = (int)(rng() % 9) - 3;  // unit 2^k
+    double d[3];
+    double r;
+    do {
+      for (double& v : d) v = U(rng) * 8.0;
+      r = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    } while (r < 1.5 || r > 13.0);
+    for (double& v : d) v = std::ldexp(v, k);  // displacement in box units
+    const double s = (c & 1) ? 1.0 : -0.25;
+    // device-order evaluation: 8 lanes, inputs in units of 2^k
+    std::vector<CX> out(16 * 16, CX(0, 0));
+    std::vector<int> hits(16 * 16, 0);
+    std::mutex omu;
+    std::vector<std::thread> th;
+    for (unsigned lane = 0; lane < 8; lane++) {
+      th.emplace_back([&, lane] {
+        t_lane = lane;
+        irregular_group_w2(A2, W2, p, f2_from_double(d[0], -k), f2_from_double(d[1], -k),
+                           f2_from_double(d[2], -k), f2_from_double(s, 0),
+                           [&](int t, int n, int m, bool v, f2 vr, f2 vi) {
+                             if (!v) return;
+                             const int e = -k * (n + 1);
+                             std::lock_guard<std::mutex> g(omu);
+                             out[n * 16 + m] = CX(f2_to_double(vr, e), f2_to_double(vi, e));
+                             hits[n * 16 + m]++;
+                           });
+      });
+    }
+    for (auto& t : th) t.join();
+    // reference: the unscaled two-term recurrence (A = 2n - 1,
+    // B = (n + m - 1)(n - m - 1)) in long double, divided by P_n^m
+    const LD x = d[0], y = d[1], z = d[2];
+    const LD r2 = x * x + y * y + z * z, ir = 1.0L / std::sqrt(r2), Q = ir * ir;
+    const CX XY(x * Q, y * Q);
+    const LD Z = z * Q;
+    CX diag = CX(ir * (LD)s, 0);
+    for (int m = 0; m <= p; m++) {
+      if (m > 0) diag *= (LD)(2 * m - 1) * XY;
+      std::vector<CX> I(p + 1);
+      LD colmax = 0;
+      for (int n = m; n <= p; n++) {
+        if (n == m) I[n] = diag;
+        else if (n == m + 1) I[n] = (LD)(2 * n - 1) * Z * I[n - 1];
+        else I[n] = (LD)(2 * n - 1) * Z * I[n - 1] - Q * (LD)((n + m - 1) * (n - m - 1)) * I[n - 2];
+      }
+      std::vector<CX> w(p + 1);
+      for (int n = m; n <= p; n++) {
+        LD P = 1;
+        for (int j = m + 1; j <= n; j++) P *= (LD)(2 * j - 1);
+        w[n] = I[n] / P;
+        colmax = std::max(colmax, std::abs(w[n]));
+      }
+      for (int n = m; n <= p; n++) {
+        if (hits[n * 16 + m] != 1) bad_cover++;
+        const LD err = std::abs(CX(out[n * 16 + m]) - w[n]) / colmax;
+        worst = std::max(worst, (double)err);
+      }
+    }
+    for (int n = 0; n < 16; n++)
+      for (int m = 0; m < 16; m++)
+        if ((m > n || n > p) && hits[n * 16 + m] != 0) bad_cover++;
+  }
+  std::printf("%.6g %d\n", worst, bad_cover);
+  return 0;
+}
+"""
+
+
+def test_pair_harmonic_group_matches_long_double_recurrence(tmp_path):
+    """irregular_group_w2 run as on the device by 8 emulated lanes (host
+    threads, shuffles through a barrier): every (n, m) with m <= n <= p made
+    exactly once, and within 1e-12 of its column's largest value against the
+    unscaled two-term recurrence in long double divided by P_n^m, over
+    random displacements with |x| in [1.5, 13] cell units, units 2^-3..2^5
+    and p = 6, 10, 12, 15."""
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("no host C++ compiler")
+    header = os.path.join(HERE, "..", "paper_2006_16622_gb300", "csrc", "mc_pair_harm.cuh")
+    src = tmp_path / "group.cpp"
+    src.write_text(GROUP_HARNESS.replace("HEADER", os.path.abspath(header)))
+    exe = tmp_path / "group"
+    r = subprocess.run([gxx, "-O2", "-std=c++17", "-ffp-contract=off", "-pthread", "-o", str(exe), str(src), "-lm"],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True, timeout=120).stdout.split()
+    worst, bad_cover = float(out[0]), int(out[1])
+    assert bad_cover == 0
+    assert worst <= 1e-12, worst
