@@ -23,6 +23,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "mc_df64.cuh"
+
 #define MC_PMAX 15
 #define MC_MAXLEV 8
 #define MC_THREADS 256
@@ -121,26 +123,6 @@ struct RunParams {
 
 #include "mc_philox.cuh"
 
-// IEEE-754 conversions on the integer pipe (the FP64 pipe is 1/64 rate).
-// float -> double is exact for normal floats; subnormal floats become 0.
-__device__ __forceinline__ double f2d_int(float f) {
-  const uint32_t b = __float_as_uint(f);
-  const uint32_t e = (b >> 23) & 0xffu;
-  const uint32_t sign = b & 0x80000000u;
-  const uint32_t hi = e ? (sign | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3)) : sign;
-  const uint32_t lo = e ? (b << 29) : 0u;
-  return __hiloint2double((int)hi, (int)lo);
-}
-// double -> float rounded toward zero; |x| beyond the float range saturates
-// to +-inf, below it flushes to 0 (branch-free).
-__device__ __forceinline__ float d2f_int(double x) {
-  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
-  const int e = (int)((hi >> 20) & 0x7ffu) - 896;
-  uint32_t mag = ((uint32_t)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
-  mag = (e <= 0) ? 0u : mag;
-  mag = (e >= 255) ? 0x7f800000u : mag;
-  return __uint_as_float((hi & 0x80000000u) | mag);
-}
 template <typename T> __device__ __forceinline__ T from_double(double x);
 template <> __device__ __forceinline__ double from_double<double>(double x) { return x; }
 template <> __device__ __forceinline__ float from_double<float>(double x) { return d2f_int(x); }

@@ -46,6 +46,14 @@ static inline double __longlong_as_double(long long x) { double r; std::memcpy(&
 static inline float __int_as_float(int x) { float r; std::memcpy(&r, &x, 4); return r; }
 static inline int __float_as_int(float x) { int r; std::memcpy(&r, &x, 4); return r; }
 static inline int __clz(unsigned x) { return x ? __builtin_clz(x) : 32; }
+static inline unsigned __float_as_uint(float x) { unsigned r; std::memcpy(&r, &x, 4); return r; }
+static inline float __uint_as_float(unsigned x) { float r; std::memcpy(&r, &x, 4); return r; }
+static inline double __hiloint2double(int hi, int lo) {
+  const unsigned long long b = ((unsigned long long)(unsigned)hi << 32) | (unsigned)lo;
+  double r; std::memcpy(&r, &b, 8); return r;
+}
+static inline int __double2hiint(double x) { unsigned long long b; std::memcpy(&b, &x, 8); return (int)(b >> 32); }
+static inline int __double2loint(double x) { unsigned long long b; std::memcpy(&b, &x, 8); return (int)(unsigned)b; }
 static inline float rsqrtf(float x) { return 1.0f / std::sqrt(x); }
 static inline double rsqrt(double x) { return 1.0 / std::sqrt(x); }
 

@@ -29,6 +29,14 @@ static inline double __longlong_as_double(long long x) { double r; std::memcpy(&
 static inline float __int_as_float(int x) { float r; std::memcpy(&r, &x, 4); return r; }
 static inline int __float_as_int(float x) { int r; std::memcpy(&r, &x, 4); return r; }
 static inline int __clz(unsigned x) { return x ? __builtin_clz(x) : 32; }
+static inline unsigned __float_as_uint(float x) { unsigned r; std::memcpy(&r, &x, 4); return r; }
+static inline float __uint_as_float(unsigned x) { float r; std::memcpy(&r, &x, 4); return r; }
+static inline double __hiloint2double(int hi, int lo) {
+  const unsigned long long b = ((unsigned long long)(unsigned)hi << 32) | (unsigned)lo;
+  double r; std::memcpy(&r, &b, 8); return r;
+}
+static inline int __double2hiint(double x) { unsigned long long b; std::memcpy(&b, &x, 8); return (int)(b >> 32); }
+static inline int __double2loint(double x) { unsigned long long b; std::memcpy(&b, &x, 8); return (int)(unsigned)b; }
 static inline float rsqrtf(float x) { return 1.0f / std::sqrt(x) * (1.0f + 2.4e-7f); }
 #define __shfl_up_sync(m, v, d, w) (v)
 #define __shfl_sync(m, v, s, w) (v)
@@ -106,6 +114,14 @@ static inline double __longlong_as_double(long long x) { double r; std::memcpy(&
 static inline float __int_as_float(int x) { float r; std::memcpy(&r, &x, 4); return r; }
 static inline int __float_as_int(float x) { int r; std::memcpy(&r, &x, 4); return r; }
 static inline int __clz(unsigned x) { return x ? __builtin_clz(x) : 32; }
+static inline unsigned __float_as_uint(float x) { unsigned r; std::memcpy(&r, &x, 4); return r; }
+static inline float __uint_as_float(unsigned x) { float r; std::memcpy(&r, &x, 4); return r; }
+static inline double __hiloint2double(int hi, int lo) {
+  const unsigned long long b = ((unsigned long long)(unsigned)hi << 32) | (unsigned)lo;
+  double r; std::memcpy(&r, &b, 8); return r;
+}
+static inline int __double2hiint(double x) { unsigned long long b; std::memcpy(&b, &x, 8); return (int)(b >> 32); }
+static inline int __double2loint(double x) { unsigned long long b; std::memcpy(&b, &x, 8); return (int)(unsigned)b; }
 static inline float rsqrtf(float x) { return 1.0f / std::sqrt(x); }
 
 // eight host threads stand for the eight lanes of one group; a shuffle is a
@@ -245,3 +261,76 @@ def test_pair_harmonic_group_matches_long_double_recurrence(tmp_path):
     worst, bad_cover = float(out[0]), int(out[1])
     assert bad_cover == 0
     assert worst <= 1e-12, worst
+
+
+CONV_HARNESS = r"""
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <cstdint>
+#include <random>
+#define __device__
+#define __forceinline__ inline
+static inline long long __double_as_longlong(double x) { long long r; std::memcpy(&r, &x, 8); return r; }
+static inline double __longlong_as_double(long long x) { double r; std::memcpy(&r, &x, 8); return r; }
+static inline float __int_as_float(int x) { float r; std::memcpy(&r, &x, 4); return r; }
+static inline int __float_as_int(float x) { int r; std::memcpy(&r, &x, 4); return r; }
+static inline unsigned __float_as_uint(float x) { unsigned r; std::memcpy(&r, &x, 4); return r; }
+static inline float __uint_as_float(unsigned x) { float r; std::memcpy(&r, &x, 4); return r; }
+static inline double __hiloint2double(int hi, int lo) {
+  const unsigned long long b = ((unsigned long long)(unsigned)hi << 32) | (unsigned)lo;
+  return __longlong_as_double((long long)b);
+}
+static inline int __double2hiint(double x) { return (int)((unsigned long long)__double_as_longlong(x) >> 32); }
+static inline int __double2loint(double x) { return (int)(unsigned)(unsigned long long)__double_as_longlong(x); }
+static inline int __clz(unsigned x) { return x ? __builtin_clz(x) : 32; }
+static inline float rsqrtf(float x) { return 1.0f / std::sqrt(x); }
+#define __shfl_up_sync(m, v, d, w) (v)
+#define __shfl_sync(m, v, s, w) (v)
+#include "HEADER"
+
+static bool same_bits(float a, float b) { return __float_as_uint(a) == __float_as_uint(b); }
+static bool same_bits(double a, double b) { return __double_as_longlong(a) == __double_as_longlong(b); }
+
+int main() {
+  std::mt19937_64 g(3);
+  int bad_f2d = 0, bad_d2f = 0;
+  for (int it = 0; it < 1000000; it++) {
+    // float -> double: exact for normal floats, subnormals to signed zero
+    const unsigned fb = (unsigned)g();
+    const float f = __uint_as_float(fb);
+    const unsigned ef = (fb >> 23) & 0xffu;
+    if (ef != 0xffu) {
+      const double want = ef ? (double)f : std::copysign(0.0, (double)f);
+      if (!same_bits(f2d_int(f), want)) bad_f2d++;
+    }
+    // double -> float toward zero, flushed below 2^-126, +-inf from 2^128
+    const double x = std::ldexp((double)((int64_t)g()) / 9.3e18, (int)(g() % 300) - 150);
+    float want = (float)x;
+    if (std::fabs((double)want) > std::fabs(x)) want = std::nextafterf(want, 0.0f);
+    if (std::fabs(x) < std::ldexp(1.0, -126)) want = std::copysign(0.0f, (float)x);
+    if (std::fabs(x) >= std::ldexp(1.0, 128)) want = std::copysign(INFINITY, (float)x);
+    if (!same_bits(d2f_int(x), want)) bad_d2f++;
+  }
+  std::printf("%d %d\n", bad_f2d, bad_d2f);
+  return 0;
+}
+"""
+
+
+def test_integer_pipe_conversions(tmp_path):
+    """f2d_int is exact for every normal float (subnormals become signed
+    zero); d2f_int rounds toward zero, flushes below 2^-126 and saturates to
+    +-inf from 2^128, bit for bit against the host's IEEE conversions."""
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("no host C++ compiler")
+    src = tmp_path / "conv.cpp"
+    src.write_text(CONV_HARNESS.replace("HEADER", os.path.abspath(HEADER)))
+    exe = tmp_path / "conv"
+    r = subprocess.run([gxx, "-O2", "-std=c++17", "-ffp-contract=off", "-o", str(exe), str(src), "-lm"],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
+    bad_f2d, bad_d2f = (int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                        text=True).stdout.split())
+    assert bad_f2d == 0 and bad_d2f == 0, (bad_f2d, bad_d2f)
