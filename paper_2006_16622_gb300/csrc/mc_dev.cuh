@@ -234,42 +234,7 @@ __device__ __forceinline__ float neg_bits(float x) { return -x; }
 __device__ __forceinline__ int rl_re(int n, int m) { return n * n + (m ? 2 * m - 1 : 0); }
 
 // ------------------------------------------------------------- geometry
-// Interaction-list offsets (Sec. 3.1) for the 8 parity classes of a cell:
-// children of the parent's 27 neighbours span [-2-b, 3-b] per axis (b the
-// cell's parity on that axis); the 27 near offsets are removed.  Built per
-// CTA in shared memory: il[parity][k] = packed (ox+4) | (oy+4)<<4 | (oz+4)<<8.
-__device__ __forceinline__ void il_table_init(unsigned short (*il)[189]) {
-  for (int t = threadIdx.x; t < 8 * 216; t += blockDim.x) {
-    const int par = t / 216, b = t % 216;
-    const int bx = (par >> 2) & 1, by = (par >> 1) & 1, bz = par & 1;
-    const int i = b / 36, jj = (b / 6) % 6, l = b % 6;
-    const int ox = i - 2 - bx, oy = jj - 2 - by, oz = l - 2 - bz;
-    const bool inner = (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1);
-    if (inner) continue;
-    // rank of b among the non-inner entries of this parity class
-    int k = 0;
-    for (int bb = 0; bb < b; bb++) {
-      const int ii = bb / 36, j2 = (bb / 6) % 6, l2 = bb % 6;
-      const int px = ii - 2 - bx, py = j2 - 2 - by, pz = l2 - 2 - bz;
-      if (!(px >= -1 && px <= 1 && py >= -1 && py <= 1 && pz >= -1 && pz <= 1)) k++;
-    }
-    il[par][k] = (unsigned short)((ox + 4) | ((oy + 4) << 4) | ((oz + 4) << 8));
-  }
-}
-__device__ __forceinline__ void il_unpack(unsigned short v, int* ox, int* oy, int* oz) {
-  *ox = (int)(v & 15) - 4;
-  *oy = (int)((v >> 4) & 15) - 4;
-  *oz = (int)((v >> 8) & 15) - 4;
-}
-
-__device__ __forceinline__ int mc_wrap_coord(int e, int n) { return ((e % n) + n) % n; }
-
-__device__ __forceinline__ bool in_il(int ox, int oy, int oz, int cx, int cy, int cz) {
-  const int bx = cx & 1, by = cy & 1, bz = cz & 1;
-  if (ox < -2 - bx || ox > 3 - bx || oy < -2 - by || oy > 3 - by || oz < -2 - bz || oz > 3 - bz)
-    return false;
-  return (ox < -1 || ox > 1 || oy < -1 || oy > 1 || oz < -1 || oz > 1);
-}
+#include "mc_geom.cuh"
 
 __device__ __forceinline__ int finest_coord(double x, double inv_w, int nL) {
   int v = (int)floor(__dmul_rn(x, inv_w));
