@@ -4,10 +4,14 @@ local-expansion electrostatics method on the uniform N=1e5 workload
 
 One bench step = one persistent launch (mc_run) of --mh-steps proposals on
 the resident system.  `value` is the FP64 form, timed with CUDA events on the
-library's stream, L2 flushed between timed steps.  The JSON line also carries
-the FP32-eval form, the setup time, the end-to-end number through the C ABI
-with host buffers, the roofline of the chain kernel and the CPU oracle
-baseline.  --impl reference times the CPU oracle instead.
+library's stream, L2 flushed between timed steps.  The last stdout line (the
+result) also carries the FP32-eval and batched forms with their roofline
+fractions, the precision form's dE error and drift, the end-to-end number
+through the C ABI with host buffers, the roofline of the chain kernel and the
+CPU oracle baseline; the line before it ("detail") holds the bulky legs
+(per-chain batch split, N = 1e6 setup-heavy case, per-operation timing
+against N, the full-MC NaCl setting).  --impl reference times the CPU oracle
+instead; --profile FORM brackets one launch for ncu.
 
 Multi-GPU: independent replicas (one chain per GPU, seed = rank), no
 collective on the data path; value = all ranks' proposals / max time.
@@ -30,6 +34,26 @@ METRIC = "MH steps/sec at N=1e5, p=12: plain FP64 vs FP32-eval/FP64-acc and batc
 UNIT = "MH steps/s"
 FP64_PEAK_FLOPS = 152 * 4 * 2.070e9  # 152 SMs x 4 FP64 flop/clk/SM (2 FMA lanes) x max clock
 FP32_PEAK_FLOPS = 152 * 256 * 2.070e9  # 152 SMs x 128 FP32 lanes x 2 flop (FMA) x max clock
+
+
+def fp_peaks_measured():
+    """FMA-pipe peaks of this GPU in flop/s (FP64, FP32), measured by the
+    library's probe (independent FMA chains on every SM, CUDA events)."""
+    from paper_2006_16622_gb300 import mcfmm
+    return mcfmm.probe_fma_rate(True, 0.2), mcfmm.probe_fma_rate(False, 0.2)
+
+
+def csrc_sha16():
+    """Hash of the CUDA sources: an ncu summary taken on other sources no
+    longer describes the kernels that run."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2006_16622_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(f.encode())
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def hbm_peak_bytes():
@@ -63,8 +87,23 @@ def parse():
                     help="run only the acceptance-probability study (relative error of P vs p)")
     ap.add_argument("--accuracy-configs", type=int, default=16)
     ap.add_argument("--accuracy-moves", type=int, default=1000)
-    ap.add_argument("--huge-steps", type=int, default=100_000,
+    ap.add_argument("--huge-steps", type=int, default=1_000_000,
                     help="proposals timed per form on the N=1e6 workload")
+    ap.add_argument("--c3-moves", type=int, default=10_000_000,
+                    help="FP32-eval proposals of the precision-form run (re-setups included)")
+    ap.add_argument("--c3-resetup", type=int, default=100_000,
+                    help="accepted moves between full FP64 re-setups in the precision-form run")
+    ap.add_argument("--c3-floor-moves", type=int, default=2_000_000,
+                    help="FP64 proposals of the drift-floor run")
+    ap.add_argument("--schedules", action="store_true",
+                    help="also time the phased FP64 and plain FP32-eval schedules")
+    ap.add_argument("--profile", default=None,
+                    choices=["fp64", "fp64_phased", "fp32_eval", "fp32_eval_async", "batched_fp64",
+                             "batched_fp32_eval", "setup_p2l", "setup_fmm"],
+                    help="build the workload, warm up, and bracket one launch with "
+                         "cudaProfilerStart/Stop (for ncu --profile-from-start off); no timing")
+    ap.add_argument("--profile-n", type=int, default=0,
+                    help="system size of --profile (0: the form's bench workload)")
     return ap.parse_args()
 
 
@@ -159,9 +198,7 @@ def batched_cpu_baseline(proposals=300):
 
 def cpu_baseline_from(res):
     return {"value": res["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"{res['sample']} proposals (after 100 warm-up) of the same chain on the "
-                       f"N=1e5 workload, FP64 oracle, one host thread; oracle setup "
-                       f"{res['setup_s']:.0f} s not timed")}
+            "sample": f"{res['sample']} proposals, setup untimed"}
 
 
 def reference_arm(args):
@@ -318,18 +355,21 @@ def bytes_per_step(p, levels, nbar, nu):
     return b_prop + nu * b_acc
 
 
-def read_profile_traffic():
-    """DRAM bytes per launch of the timed chain kernel (the barrier-free FP64
-    chain, 50 000 proposals) from the committed ncu summary of one full
-    launch, or None."""
-    path = os.path.join(ROOT, "profiles", "async_fp64_dram_full_launch_N1e5.md")
+def read_profile_traffic(name="async_fp64_dram_full_launch_N1e5.md"):
+    """DRAM bytes per launch of the timed chain kernel (50 000 proposals)
+    from the committed ncu summary of one full launch, when that summary was
+    taken on the current CUDA sources (its `csrc_sha16:` line), else None."""
+    path = os.path.join(ROOT, "profiles", name)
+    traffic, sha = None, None
     try:
         for line in open(path):
             if line.startswith("dram_bytes_per_launch:"):
-                return float(line.split(":")[1].split()[0])
+                traffic = float(line.split(":")[1].split()[0])
+            elif line.startswith("csrc_sha16:"):
+                sha = line.split(":")[1].strip()
     except (OSError, ValueError, IndexError):
-        pass
-    return None
+        return None
+    return traffic if sha == csrc_sha16() else None
 
 
 def batched_form(args, precision, stream, flush):
@@ -487,7 +527,7 @@ def size_sweep_leg(stream):
 
 
 def nacl_full_mc_leg(stream):
-    """The paper's full Monte Carlo setting (Sec. 5.4): 46^3 NaCl ions in a
+    """The paper's full Monte Carlo setting (Sec. 5.3): 46^3 NaCl ions in a
     153.2 A box, 12 expansion terms (p = 11), L = 4, T = 273 K, moves of
     +-0.25 A, with the short-range Lennard-Jones term (12 A cutoff); MH
     steps/s of both methods (FP64) over 20 000 proposals."""
@@ -521,41 +561,175 @@ def nacl_full_mc_leg(stream):
     return out
 
 
-def precision_form_stats(W, stream):
-    """FP32-eval vs the (oracle-parity-tested) FP64 chain on the same seed:
-    per-proposal dE error over the common prefix of the two chains, and the
-    energy drift with a full FP64 re-setup every R accepts, next to the FP64
-    drift floor (P2L truncation asymmetry)."""
+def _dE_error_vs_fp64(pos, q, W, stream, seed, steps=4000):
+    """FP32-eval against the (oracle-parity-tested) FP64 chain from the same
+    state and seed: |dE_fp32 - dE_fp64| over the common prefix (until the
+    first differing decision) of `steps` logged proposals."""
     import numpy as np
 
     from paper_2006_16622_gb300 import mcfmm
-    pos, q = W.system()
-    out = {}
-    M = 4000
     logs = {}
     for prec in (mcfmm.FP64, mcfmm.FP32_EVAL):
         c = mcfmm.Context(pos, q, W.a, W.levels, W.p, precision=prec, stream=stream.cuda_stream)
         c.setup()
-        logs[prec] = c.run(M, seed=77, beta=W.beta, half_width=W.half_width, log=True)
+        logs[prec] = c.run(steps, seed=seed, beta=W.beta, half_width=W.half_width, log=True)
         c.close()
     a64, a32 = logs[mcfmm.FP64], logs[mcfmm.FP32_EVAL]
     diff = np.nonzero(a64["acc"] != a32["acc"])[0]
-    k = int(diff[0]) if len(diff) else M
-    e = np.abs(a32["dE"][:k] - a64["dE"][:k])
-    e = e[np.isfinite(e)]
-    out.update(dE_err_p95=float(np.percentile(e, 95)), dE_err_max=float(e.max()),
-               dE_err_samples=int(len(e)), common_prefix=k)
-    R = 50_000
-    for name, prec in (("fp32_eval", mcfmm.FP32_EVAL), ("fp64_floor", mcfmm.FP64)):
+    k = int(diff[0]) if len(diff) else steps
+    e = W.beta * np.abs(a32["dE"][:k] - a64["dE"][:k])
+    return e[np.isfinite(e)]
+
+
+def precision_form_leg(args, W, stream):
+    """The precision form as configured: --c3-moves FP32-eval proposals on
+    the N = 1e5 workload with a full FP64 re-setup every --c3-resetup
+    accepted moves (one mc_run call; wall time includes the re-setups), the
+    running-minus-fresh energy drift at every re-setup per 1e6 accepts, next
+    to the FP64 form's drift floor (P2L truncation asymmetry) over
+    --c3-floor-moves; the dE error against the FP64 chain at the start and
+    from the FP32-eval chain's final state (4000 proposals each)."""
+    import numpy as np
+
+    from paper_2006_16622_gb300 import mcfmm
+    pos, q = W.system()
+    R = args.c3_resetup
+    out = {"moves": args.c3_moves, "resetup_every_accepts": R}
+    final_pos = None
+    for name, prec, moves in (("fp32_eval", mcfmm.FP32_EVAL, args.c3_moves),
+                              ("fp64_floor", mcfmm.FP64, args.c3_floor_moves)):
         c = mcfmm.Context(pos, q, W.a, W.levels, W.p, precision=prec, stream=stream.cuda_stream)
         c.setup()
-        st = c.run(int(2.2 * R / 0.9), seed=78, beta=W.beta, half_width=W.half_width,
-                   resetup_every=R)
+        stream.synchronize()
+        t0 = time.perf_counter()
+        st = c.run(moves, seed=78, beta=W.beta, half_width=W.half_width, resetup_every=R)
+        dt = time.perf_counter() - t0
+        if name == "fp32_eval":
+            final_pos = c.positions()
+        status = c.status()
         c.close()
-        out[f"drift_per_1e6_accepts_{name}"] = st["max_drift"] * 1e6 / R
-        out[f"resetups_{name}"] = st["resetups"]
-    out["resetup_every_accepts"] = R
+        if status != 0 or st["steps"] != moves:
+            raise RuntimeError(f"precision-form chain status {status}")
+        k = max(1, st["resetups"])
+        out[name] = {"mh_steps_per_s": moves / dt, "accepted": st["accepted"],
+                     "resetups": st["resetups"],
+                     "drift_max_per_1e6_acc": st["max_drift"] * 1e6 / R,
+                     "drift_mean_abs_per_1e6_acc": st["sum_abs_drift"] / k * 1e6 / R,
+                     "drift_mean_signed_per_1e6_acc": st["sum_drift"] / k * 1e6 / R}
+    e = np.concatenate([_dE_error_vs_fp64(pos, q, W, stream, seed=77),
+                        _dE_error_vs_fp64(final_pos, q, W, stream, seed=79)])
+    out.update(dE_err_p95=float(np.percentile(e, 95)), dE_err_max=float(e.max()),
+               dE_err_samples=int(len(e)))
     return out
+
+
+def profile_launch(args):
+    """One launch of the chosen form bracketed by cudaProfilerStart/Stop, so
+    that `ncu --profile-from-start off -k regex:<kernel> -c 1` captures it
+    after the untimed warm-up launches.  Chains: --mh-steps proposals on the
+    N = 1e5 workload (or --profile-n charges at density 0.1); batches: the
+    64-chain batched workload, tuned, --batch-steps proposals per chain;
+    setups: one setup pass of --profile-n charges (default 1e5) at density
+    0.1, ~20-30 charges per finest cell, p = 12."""
+    import numpy as np
+    import torch
+
+    from paper_2006_16622_gb300 import mcfmm
+    from paper_2006_16622_gb300.workloads import LARGE, batched_systems, size_sweep, uniform_system
+
+    mcfmm.load()
+    form = args.profile
+    ok = True
+    if form.startswith("batched"):
+        prec = mcfmm.FP64 if form == "batched_fp64" else mcfmm.FP32_EVAL
+        ctxs = []
+        for n, a, L, i in batched_systems(64, 1000, 50000, 0.1, 20.0):
+            pos, q = uniform_system(n, a, seed=1000 + i)
+            c = mcfmm.Context(pos, q, a, L, 10, precision=prec)
+            c.setup()
+            ctxs.append(c)
+        b = mcfmm.Batch(ctxs)
+        b.tune(trial_steps=300, beta=1.0, half_width=0.3)
+        seeds = np.arange(len(ctxs), dtype=np.uint64)
+        for _ in range(3):
+            b.run(args.batch_steps, seeds, beta=1.0, half_width=0.3, stats=False)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        b.run(args.batch_steps, seeds, beta=1.0, half_width=0.3, stats=False)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        ok = all(c.status() == 0 for c in ctxs)
+        b.close()
+        for c in ctxs:
+            c.close()
+    else:
+        W = LARGE if args.profile_n == 0 else size_sweep((args.profile_n,))[0]
+        if form.startswith("setup") and args.profile_n == 0:
+            W = LARGE
+        pos, q = W.system()
+        prec = mcfmm.FP32_EVAL if form.startswith("fp32") else mcfmm.FP64
+        c = mcfmm.Context(pos, q, W.a, W.levels, W.p, precision=prec)
+        if form.startswith("setup"):
+            mode = mcfmm.SETUP_P2L if form == "setup_p2l" else mcfmm.SETUP_FMM
+            c.setup(mode)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.start()
+            c.setup(mode)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
+        else:
+            c.setup()
+            if form == "fp64_phased":
+                c.set_schedule(mcfmm.SCHEDULE_PHASED)
+            elif form == "fp32_eval_async":
+                c.set_schedule(mcfmm.SCHEDULE_ASYNC)
+            for _ in range(3):
+                c.run(args.mh_steps, seed=W.seed, beta=W.beta, half_width=W.half_width, stats=False)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.start()
+            c.run(args.mh_steps, seed=W.seed, beta=W.beta, half_width=W.half_width, stats=False)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
+        ok = c.status() == 0
+        c.close()
+    print(json.dumps({"profile": form, "ok": ok, "mh_steps": args.mh_steps,
+                      "batch_steps": args.batch_steps, "n": args.profile_n}), flush=True)
+    if not ok:
+        sys.exit(1)
+
+
+def compact_line(value, ms_per_step, args, world, r64, e2e, roof, cpu, forms, fr, prec_stats,
+                 workload):
+    """The result line: the contract's keys, the three forms with their
+    roofline fractions and the precision form's summary; the bulky legs go
+    on the line before it."""
+    def rnd(x, k=4):
+        if isinstance(x, float):
+            return float(f"{x:.{k}g}")
+        if isinstance(x, dict):
+            return {kk: rnd(v, k) for kk, v in x.items()}
+        return x
+    line = {"metric": METRIC, "value": rnd(value, 7), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": rnd(ms_per_step, 6),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload, "l2": "flushed", "parallelism": f"replicas x{world}"},
+            "roofline": {k: rnd(v) for k, v in roof.items()
+                         if k not in ("traffic_source", "flops_per_mh_step", "acceptance")},
+            "cpu_baseline": rnd(cpu) if cpu else None,
+            "e2e": {k: rnd(v) for k, v in e2e.items() if k != "what"} if e2e else None,
+            "gpu_launches": args.steps,
+            "clocks": ({k: rnd(v) for k, v in r64["clocks"].items() if k != "samples"}
+                       if r64["clocks"] else None),
+            "forms": rnd(forms), "roofline_frac": rnd(fr, 3)}
+    if prec_stats:
+        line["precision_form"] = {
+            "moves": prec_stats["moves"], "resetups": prec_stats["fp32_eval"]["resetups"],
+            "rate": rnd(prec_stats["fp32_eval"]["mh_steps_per_s"]),
+            "drift_1e6acc": rnd(prec_stats["fp32_eval"]["drift_mean_abs_per_1e6_acc"], 3),
+            "floor_1e6acc": rnd(prec_stats["fp64_floor"]["drift_mean_abs_per_1e6_acc"], 3),
+            "dE_p95": rnd(prec_stats["dE_err_p95"], 2), "dE_max": rnd(prec_stats["dE_err_max"], 2)}
+    return line
 
 
 def gpu_arm(args):
@@ -584,6 +758,7 @@ def gpu_arm(args):
     pos, q = W.system()
     S = args.mh_steps
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    fp64_meas, fp32_meas = fp_peaks_measured()
 
     def time_form(precision, schedule=None):
         # schedule None: the context's default (barrier-free for FP64,
@@ -630,17 +805,18 @@ def gpu_arm(args):
         return dict(total=tot, durs=durs, setup_s=setup_s, nu=nu, clocks=clocks)
 
     r64 = time_form(mcfmm.FP64)
-    r64p = r32 = r32p = None
+    r32 = r64p = r32p = None
     if not args.no_fp32:
-        r64p = time_form(mcfmm.FP64, mcfmm.SCHEDULE_PHASED)
         r32 = time_form(mcfmm.FP32_EVAL)
-        r32p = time_form(mcfmm.FP32_EVAL, mcfmm.SCHEDULE_PLAIN)
+        if args.schedules:
+            r64p = time_form(mcfmm.FP64, mcfmm.SCHEDULE_PHASED)
+            r32p = time_form(mcfmm.FP32_EVAL, mcfmm.SCHEDULE_PLAIN)
 
     rb32 = rb64 = None
     if not args.no_batch:
         rb32 = batched_form(args, mcfmm.FP32_EVAL, stream, flush)
         rb64 = batched_form(args, mcfmm.FP64, stream, flush)
-    prec_stats = None if args.no_precision else precision_form_stats(W, stream)
+    prec_stats = None if (args.no_precision or rank != 0) else precision_form_leg(args, W, stream)
     huge = None if (args.no_huge or rank != 0) else huge_workload_leg(args, stream, flush)
     sweep = None if (args.no_sweep or rank != 0) else size_sweep_leg(stream)
     nacl = None if (args.no_nacl or rank != 0) else nacl_full_mc_leg(stream)
@@ -666,8 +842,7 @@ def gpu_arm(args):
         e2e = {"value": whole_job_rate(S, world, te), "unit": UNIT,
                "h2d_bytes_per_step": int(pos.nbytes + q.nbytes),
                "d2h_bytes_per_step": int(len(q) * 32 + 8),
-               "what": "per step: mc_init from host arrays, mc_setup, mc_run, positions + energy "
-                       "copied back, mc_destroy"}
+               "what": "mc_init from host arrays, mc_setup, mc_run, positions+energy back, mc_destroy"}
 
     if rank != 0:
         return
@@ -678,12 +853,11 @@ def gpu_arm(args):
     achieved = F * S / per_launch
     traffic_launch = read_profile_traffic() if S == 50_000 else None
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
-            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_FLOPS,
-            "traffic": traffic_launch,
+            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_FLOPS, "traffic": traffic_launch,
+            "traffic_source": "ncu summary of one full launch (profiles/), null if taken on other sources",
             "kernel": "mc_async_kernel<double>",
-            "peak_source": "derived from unit counts: 152 SMs x 4 FP64 flop/clk x 2070 MHz",
-            "flops_per_mh_step": F, "bytes_per_mh_step": bytes_per_step(W.p, W.levels, nbar, r64["nu"]),
-            "acceptance": r64["nu"]}
+            "peak_source": "derived", "peak_measured": fp64_meas / 1e12, "frac_of_measured": achieved / fp64_meas,
+            "flops_per_mh_step": F, "acceptance": r64["nu"]}
     cpu = None
     if oracle_proc is not None:
         proc, qq = oracle_proc
@@ -702,20 +876,24 @@ def gpu_arm(args):
             cpu_batched = {"value": None, "unit": UNIT, "kind": "oracle",
                            "sample": f"batched oracle leg failed: {ex!r}"}
     forms = {"fp64": value}
+    detail = {"mh_steps_per_step": S, "fp64_setup_s": r64["setup_s"],
+              "roofline_flops_per_mh_step": F, "fp64_acceptance": r64["nu"],
+              "peaks_measured_tflops": {"fp64": fp64_meas / 1e12, "fp32": fp32_meas / 1e12}}
     if r32:
-        forms["fp64_phased_schedule"] = whole_job_rate(S * args.steps, world, r64p["total"])
         forms["fp32_eval"] = whole_job_rate(S * args.steps, world, r32["total"])
-        forms["fp32_eval_plain_schedule"] = whole_job_rate(S * args.steps, world, r32p["total"])
-        forms["fp32_eval_acceptance"] = r32["nu"]
-        forms["fp32_eval_setup_s"] = r32["setup_s"]
+        detail["fp32_eval_acceptance"] = r32["nu"]
+        detail["fp32_eval_setup_s"] = r32["setup_s"]
+    if r64p:
+        detail["fp64_phased_schedule"] = whole_job_rate(S * args.steps, world, r64p["total"])
+        detail["fp32_eval_plain_schedule"] = whole_job_rate(S * args.steps, world, r32p["total"])
     if sweep:
         row = [r for r in sweep if r["n"] == W.n]
         if row:
             forms["multipole_fp64"] = world * row[0]["multipole_fp64_mh_steps_per_s"]
     if rb32:
-        forms["batched_fp32_eval"] = world * rb32["value"]
         forms["batched_fp64"] = world * rb64["value"]
-        forms["batched_config"] = {
+        forms["batched_fp32_eval"] = world * rb32["value"]
+        detail["batched_config"] = {
             "workload": "64 chains, N log-uniform [1000, 50000], rho=0.1, ~20 per finest cell, "
                         "p=10, h=0.3, beta=1, seed i for chain i",
             "proposals_per_chain_per_step": args.batch_steps, "ctas_per_chain": rb32["ctas"],
@@ -724,8 +902,6 @@ def gpu_arm(args):
             "acceptance": rb32["acceptance"],
             "fp64_arithmetic": "FP64, except the speculative contributions' irregular recurrence in "
                                "pair-of-floats arithmetic (~46 bits) on the FP32 pipe; FP64 accumulators"}
-    else:
-        forms["batched_fp32_eval"] = None
     # every form as a fraction of its roofline (rate x speed-of-light step time)
     bw, bw_src = hbm_peak_bytes()
     fr = {"fp64": value * roofline_step_time(W.p, W.levels, nbar, r64["nu"], False)}
@@ -736,27 +912,22 @@ def gpu_arm(args):
             ts = [roofline_step_time(10, L, n / 8 ** (L - 1), rb["acceptance"], f32)
                   for n, L in zip(rb["sizes"], rb["levels"])]
             fr[key] = forms[key] * statistics.mean(ts)
-    fr["peaks"] = (f"FP64 {FP64_PEAK_FLOPS / 1e12:.2f} and FP32 {FP32_PEAK_FLOPS / 1e12:.1f} TFLOP/s derived "
-                   f"(unit counts x 2070 MHz), HBM {bw / 1e9:.0f} GB/s {bw_src}")
-    forms["roofline_frac"] = fr
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1000 * r64["total"] / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": W.name, "mh_steps_per_step": S, "form": "fp64",
-                       "schedule": "barrier-free (MC_SCHEDULE_ASYNC)",
-                       "fp32_eval_schedule": "phased (speculative accept contributions)",
-                       "l2": "flushed between timed steps (256 MiB write)",
-                       "parallelism": f"replicas x{world}"},
-            "roofline": roof, "cpu_baseline": cpu, "cpu_baseline_batched": cpu_batched, "e2e": e2e,
-            "paper_context": {"value": 1000.0, "unit": UNIT, "hardware": "1 core of an Intel Xeon E5-2650v2",
-                              "workload": "NaCl-like, N ~ 1e5, 12 expansion terms (p = 11), L = 4, periodic, "
-                                          "with Lennard-Jones",
-                              "note": "the paper's cost of about 1 ms per MH step with up to 1e5 charges (Sec. 2; "
-                                      "setting of Sec. 5.3): context only, another machine and workload"},
-            "gpu_launches": args.steps, "clocks": r64["clocks"], "forms": forms,
-            "precision_form": prec_stats,
-            "setup_s": r64["setup_s"], "huge": huge, "size_sweep": sweep, "nacl_full_mc": nacl}
+    detail["roofline_peaks"] = (f"FP64 {FP64_PEAK_FLOPS / 1e12:.2f} and FP32 {FP32_PEAK_FLOPS / 1e12:.1f} "
+                                f"TFLOP/s derived (unit counts x 2070 MHz), HBM {bw / 1e9:.0f} GB/s {bw_src}")
+    detail.update(cpu_baseline_batched=cpu_batched, precision_form=prec_stats, huge=huge,
+                  size_sweep=sweep, nacl_full_mc=nacl,
+                  paper_context={"value": 1000.0, "unit": UNIT,
+                                 "hardware": "1 core of an Intel Xeon E5-2650v2",
+                                 "workload": "NaCl-like, N ~ 1e5, 12 expansion terms (p = 11), L = 4, "
+                                             "periodic, with Lennard-Jones",
+                                 "note": "the paper's cost of about 1 ms per MH step (Sec. 2; setting "
+                                         "of Sec. 5.3): context only, another machine and workload"})
+    if huge:
+        forms["n1e6_fp64"] = huge["fp64_mh_steps_per_s"]
+        forms["n1e6_fp32_eval"] = huge["fp32_eval_mh_steps_per_s"]
+    print(json.dumps({"detail": detail}), flush=True)
+    line = compact_line(value, 1000 * r64["total"] / args.steps, args, world, r64, e2e, roof, cpu,
+                        forms, fr, prec_stats, W.name)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -817,6 +988,9 @@ def main():
     args = parse()
     if args.accuracy:
         accuracy_study(args)
+        return
+    if args.profile:
+        profile_launch(args)
         return
     if args.impl == "reference":
         reference_arm(args)

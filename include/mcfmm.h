@@ -40,9 +40,10 @@ extern "C" {
 #define MC_ERR_STATE (-10)     /* call out of order (e.g. propose before setup) */
 #define MC_ERR_NOMEM (-11)     /* device allocation failed */
 #define MC_ERR_SCRATCH (-12)   /* request larger than the fixed no-allocation scratch */
+#define MC_ERR_PENDING (-13)   /* a CUDA error of earlier work was pending at the call */
 
-#define MC_BC_PBC 0   /* periodic cube (paper Sec. 3.3) */
-#define MC_BC_FREE 1  /* free space (paper Sec. 3.3, first paragraph) */
+#define MC_BC_PBC 0   /* periodic cube (paper Sec. 3.4) */
+#define MC_BC_FREE 1  /* free space (paper Sec. 3.4, first paragraph) */
 #define MC_TINFOIL 0  /* conducting surroundings: dipole term removed */
 #define MC_VACUUM 1   /* cubic-shell (vacuum) summation of the images */
 #define MC_FP64 0     /* every step in FP64 */
@@ -53,7 +54,7 @@ extern "C" {
                           multipoles, then multipole-to-local over the
                           interaction lists; equal to MC_SETUP_P2L up to the
                           multipole truncation */
-#define MC_SETUP_MULTIPOLE 2 /* the multipole method (Sec. 3.2, alternative
+#define MC_SETUP_MULTIPOLE 2 /* the multipole method (Sec. 3.3, alternative
                           algorithm): Alg. M.3; the context then proposes and
                           accepts with Alg. M.1/M.2 (a later MC_SETUP_P2L or
                           MC_SETUP_FMM switches back to the local method) */
@@ -67,6 +68,8 @@ typedef struct {
   int64_t resetups;   /* full re-setups done by the last mc_run */
   double energy;      /* running total energy after the run */
   double max_drift;   /* max |running - fresh| energy seen at a re-setup */
+  double sum_drift;   /* sum of (running - fresh) over the re-setups */
+  double sum_abs_drift; /* sum of |running - fresh| over the re-setups */
 } mc_stats;
 
 /* Create a context (paper Sec. 4, the MCFMM_LM constructor).
@@ -84,24 +87,26 @@ int mc_init(mc_ctx **out, int64_t n, const double *pos, const double *q, double 
             int levels, int p, int bc, int dipole_bc, int precision, void *cuda_stream);
 
 /* Alg. L.3 (initialise local expansions), the box multipole K/E of
- * Sec. 3.3 (ii), the lattice local expansion H = R(K) and the total energy.
+ * Sec. 3.4 (ii), the lattice local expansion H = R(K) and the total energy.
  * mode: MC_SETUP_P2L (exact P2L of every charge) or MC_SETUP_FMM (the
  * O(p^4 N) FMM variant; allocates its multipole and offset tables on first
  * use).  Synchronous. */
 int mc_setup(mc_ctx *ctx, int mode);
 
-/* Alg. L.1 with Alg. 1 and the periodic terms of Sec. 3.3: the energy change
+/* Alg. L.1 with Alg. 1 and the periodic terms of Sec. 3.4: the energy change
  * of moving charge j (0 <= j < n) to r_new in [0, a)^3.  Writes +inf when
  * r_new coincides with another charge.  Synchronous. */
 int mc_propose(mc_ctx *ctx, int64_t j, const double r_new[3], double *dE_out);
 
-/* Alg. L.2 with the K/E update of Sec. 3.3 (iii): accept the move of j to
+/* Alg. L.2 with the K/E update of Sec. 3.4 (iii): accept the move of j to
  * r_new.  dE_or_null: the energy change to add to the running energy; NULL
  * recomputes it with Alg. L.1 first (as the paper's accept() does). */
 int mc_accept(mc_ctx *ctx, int64_t j, const double r_new[3], const double *dE_or_null);
 
-/* Metropolis-Hastings chain of n_steps proposals in one persistent launch.
- * Proposal t (global step counter s, which continues across calls) draws
+/* Metropolis-Hastings chain of n_steps proposals in one persistent launch:
+ * the user loop of Sec. 4.1 (propose(), then accept() when the move is
+ * taken) run on the device, each proposal by Alg. L.1 and each accept by
+ * Alg. L.2.  Proposal t (global step counter s, which continues across calls) draws
  * j, a displacement uniform in [-h, h]^3 and u uniform in [0, 1) from
  * Philox4x32-10 keyed by seed; the move is accepted iff dE <= 0 or
  * log(u) < -beta dE.  resetup_every_accepts > 0 re-runs mc_setup after that
@@ -113,11 +118,19 @@ int mc_run(mc_ctx *ctx, int64_t n_steps, uint64_t seed, double beta, double half
            int64_t resetup_every_accepts, mc_stats *stats, int64_t *log_j, double *log_dE,
            uint8_t *log_acc);
 
-/* Running total energy (setup energy plus accepted changes). */
+/* The chain's global step counter s: proposals made so far by mc_run and
+ * mc_batch_run (autotuning runs included) on this context; the next proposal
+ * draws Philox counter s.  Lets a caller resume or re-draw the chain
+ * elsewhere (Sec. 4.1 leaves the driver loop, and so its random stream, to
+ * the user). */
+int mc_step_counter(mc_ctx *ctx, int64_t *out);
+/* Running total energy (setup energy plus accepted changes): the energy
+ * the Sec. 4.1 interface tracks through the dE of each accept(). */
 int mc_energy(mc_ctx *ctx, double *e_out);
 /* Total energy recomputed from the current expansions and positions. */
 int mc_energy_fresh(mc_ctx *ctx, double *e_out);
-/* Current positions (n, 3) into a host array. */
+/* Current positions (n, 3) into a host array: the PositionDat r that
+ * accept() updates in Sec. 4.1. */
 int mc_get_positions(mc_ctx *ctx, double *pos_out);
 /* Local coefficients L^Delta of level l (2..L), all cells, real layout,
  * paper normalisation; host array of 8^(l-1) * (p+1)^2 doubles. */
@@ -126,13 +139,12 @@ int mc_get_local(mc_ctx *ctx, int level, double *out);
  * normalisation; host arrays of (p+1)^2 doubles (zeros for MC_BC_FREE). */
 int mc_get_far(mc_ctx *ctx, double *K_out, double *H_out);
 /* Short-range Lennard-Jones pair term 4 eps((sigma/r)^12 - (sigma/r)^6) for
- * r < cutoff between different particles (Sec. 5.4: the paper adds a
+ * r < cutoff between different particles (Sec. 5.3: the paper adds a
  * repulsive Lennard-Jones potential with a 12 Angstrom cutoff to its full
  * MC runs and gives no parameters); eps = 0 switches it off.  The cutoff may
  * not exceed the finest cell width (every pair in range is then a near-cell
  * pair of Alg. 1), else MC_ERR_ARG.  Call mc_setup again afterwards
- * (MC_ERR_STATE until then).  Not applied by MC_SCHEDULE_PIPELINED, which
- * falls back to the phased schedule while it is on. */
+ * (MC_ERR_STATE until then). */
 int mc_set_lj(mc_ctx *ctx, double eps, double sigma, double cutoff);
 /* Multipoles M_n^m of Eq. (4) of every cell of `level` (multipole method
  * only, else MC_ERR_STATE), layout as mc_get_local. */
@@ -148,13 +160,9 @@ int mc_lattice_sums(int lmax, double *out);
  *                          the proposed move are computed during the
  *                          proposal phase, on the warps the proposal leaves
  *                          idle, and only added after the decision;
- *   MC_SCHEDULE_PIPELINED  the accept of step k runs in the same phase as the
- *                          proposal of step k+1 (one barrier per step); the
- *                          proposal sees the accepted state through
- *                          speculative coarse-level deltas and exact
- *                          Legendre-series corrections.  Same results to
- *                          roundoff; slower on GB300 in the measurements so
- *                          far (contention of the merged phase);
+ *   MC_SCHEDULE_PIPELINED  withdrawn (slower than MC_SCHEDULE_PHASED in every
+ *                          measurement on GB300); its value is refused with
+ *                          MC_ERR_ARG;
  *   MC_SCHEDULE_PLAIN      (default for FP32-eval batches) as PHASED, with
  *                          the Alg. L.2 contributions computed after the
  *                          decision (no work on rejected moves);
@@ -247,6 +255,15 @@ int mc_batch_info(mc_batch *b, int *ctas_out, int *nf_cols_out);
 int mc_batch_set_schedule(mc_batch *b, int schedule);
 void mc_batch_destroy(mc_batch *b);
 
+/* Measured peak rate of the fused multiply-add pipe of the current device
+ * (fp64 != 0: FP64, else FP32), in flop/s (2 per FMA): independent FMA
+ * chains on every SM, timed with CUDA events, the loop grown until one
+ * launch lasts about target_seconds (0 < target_seconds <= 10), best of three.
+ * The denominator of the roofline of the ALU-bound chain kernels.  A
+ * measurement helper; the paper has no counterpart.  Synchronous; allocates
+ * and frees a small output buffer. */
+int mc_probe_fma_rate(int fp64, double target_seconds, double *flops_out);
+
 /* Size of the fixed device scratch of mc_p2l_level_noalloc, in doubles
  * (8 MiB), held by every GPU that loads the library until the process exits. */
 #define MC_NOALLOC_SCRATCH_DOUBLES (1 << 20)
@@ -258,13 +275,15 @@ void mc_batch_destroy(mc_batch *b);
  * byte of device memory from its own pool, code running where an allocation
  * would synchronise the device or is forbidden, embedders that audit hidden
  * allocations.  It computes the same coefficients as mc_setup + mc_get_local
- * for one level (the gather form of Alg. L.3), from buffers the caller owns:
+ * give for one level, from buffers the caller owns:
  *   d_part        device, n rows of (x, y, z, q) doubles, grouped by finest
  *                 cell (levels L: 2^(L-1) cells per axis, cell of a point =
  *                 floor(x 2^(L-1) / box) clamped, linear index (i n + j) n + k);
  *   d_cell_start  device, 8^(L-1) + 1 ints: the charges of finest cell c are
  *                 rows [d_cell_start[c], d_cell_start[c+1]) of d_part;
- *   n, box, levels, p, bc  as for mc_init; 2 <= level <= levels;
+ *   n             rows of d_part (>= 0); informational: only checked for
+ *                 sign, the cell offsets alone decide which rows are read;
+ *   box, levels, p, bc  as for mc_init; 2 <= level <= levels;
  *   d_out         device, 8^(level-1) * (p+1)^2 doubles, written in the real
  *                 layout and paper normalisation of mc_get_local;
  *   cuda_stream   stream to launch on (NULL = legacy stream); the call only
@@ -273,11 +292,15 @@ void mc_batch_destroy(mc_batch *b);
  * MC_NOALLOC_SCRATCH_DOUBLES doubles.  A level whose 8^(level-1) (p+1)^2
  * coefficients exceed it is refused with MC_ERR_SCRATCH before any launch.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the one array: each call
- * writes every scratch value it reads before reading it, so nothing needs
- * clearing, but calls whose work overlaps on the GPU (other streams, other
- * host threads) race on it and must be serialised by the caller. */
+ * (cudaGetSymbolAddress) with that device current and keeps it for the rest
+ * of the process; make that first call before any stream capture, and make
+ * no call after a cudaDeviceReset of that device (the kept address is then
+ * stale).  Every call shares the one array: each call writes every scratch
+ * value it reads before reading it, so nothing needs clearing, but calls
+ * whose work overlaps on the GPU (other streams, other host threads) race on
+ * it and must be serialised by the caller.  A CUDA error left pending by
+ * earlier, unrelated work is neither cleared nor reported as this call's own:
+ * the call then launches nothing and returns MC_ERR_PENDING. */
 int mc_p2l_level_noalloc(const double *d_part, const int *d_cell_start, int64_t n, double box,
                          int levels, int level, int p, int bc, double *d_out, void *cuda_stream);
 

@@ -3,7 +3,7 @@
 
 TEST INFRASTRUCTURE ONLY.  The oracle is the plain, slow, single-threaded FP64
 implementation of Algorithms L.1-L.3, Algorithm 1 and the periodic extensions
-of Sec. 3.3, written from the paper.  Only ``tests/``, ``__graft_entry__.smoke``
+of Sec. 3.4, written from the paper.  Only ``tests/``, ``__graft_entry__.smoke``
 and the CPU-baseline legs of ``bench.py`` may import it; the product path
 (the CUDA library and its binding) never does.
 
@@ -94,6 +94,9 @@ def lib():
             L.orc_run.restype = _I64
             L.orc_run.argtypes = [_P, _I64, ctypes.c_uint64, ctypes.c_uint64,
                                   ctypes.c_uint32, _D, _D, _P, _P, _P, _P]
+            L.orc_run_follow.restype = _I64
+            L.orc_run_follow.argtypes = [_P, _I64, ctypes.c_uint64, ctypes.c_uint64,
+                                         ctypes.c_uint32, _D, _D, _P, _P, _P, _P, _P]
             L.orc_interaction_list.restype = ctypes.c_int
             L.orc_interaction_list.argtypes = [_P, ctypes.c_int, _P, _P]
             L.orc_ewald_energy.restype = _D
@@ -296,4 +299,17 @@ class System:
         nacc = lib().orc_run(self._h, n_steps, seed, step0, chain, beta, half_width,
                              _ptr(lj) if log else None, _ptr(ld) if log else None,
                              _ptr(la) if log else None, _ptr(nb))
+        return dict(n_acc=int(nacc), n_borderline=int(nb[0]), j=lj, dE=ld, acc=la)
+
+    def run_follow(self, follow, seed, step0=0, chain=0, beta=1.0, half_width=0.5):
+        """The chain of ``run`` with step t accepted iff follow[t] (the
+        decisions of another chain); ``acc`` holds this chain's own rule."""
+        f = np.ascontiguousarray(np.asarray(follow, dtype=np.uint8))
+        n_steps = len(f)
+        lj = np.zeros(n_steps, dtype=np.int64)
+        ld = np.zeros(n_steps)
+        la = np.zeros(n_steps, dtype=np.uint8)
+        nb = np.zeros(1, dtype=np.int64)
+        nacc = lib().orc_run_follow(self._h, n_steps, seed, step0, chain, beta, half_width,
+                                    _ptr(f), _ptr(lj), _ptr(ld), _ptr(la), _ptr(nb))
         return dict(n_acc=int(nacc), n_borderline=int(nb[0]), j=lj, dE=ld, acc=la)

@@ -10,7 +10,7 @@
  *   - Alg. L.1 (propose), Alg. 1 (direct part)                 -> orc_propose
  *   - Alg. L.2 (accept)                                        -> orc_accept
  *   - Alg. L.3 (initialise)                                    -> orc_setup
- *   - Sec. 3.3 periodic extensions: extended domain of 3^3 box copies, K/E
+ *   - Sec. 3.4 periodic extensions: extended domain of 3^3 box copies, K/E
  *     initialise/accept/propose updates, image self-interaction correction
  * Readings where the paper is silent (normalisation of Y_n^m, the lattice
  * operator R, the energy factor 1/2, the dipole boundary term, the MH rule
@@ -253,7 +253,7 @@ void orc_m2l(int p, const double *M, const double c[3], double *Lout) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Lattice sums for the far field outside the extended domain (Sec. 3.3):
+/* Lattice sums for the far field outside the extended domain (Sec. 3.4):
  *   S_l^m = sum_{v in Z^3, max|v_i| >= 2} Y_l^m(v/|v|) / |v|^(l+1).
  * Reading (the operator R is only defined in the paper's reference
  * Saunders2019): images are summed in growing cubic shells.  Then l = 1 and
@@ -368,11 +368,11 @@ struct orc_sys {
   int *cell_of;
   /* per-level local coefficients L^Delta_{l,alpha}, index [l][cell*C + IDX] */
   cplx *Lx[16];
-  /* multipole method (Sec. 3.2, alternative algorithm): per-level multipole
+  /* multipole method (Sec. 3.3, alternative algorithm): per-level multipole
    * coefficients M_{l,alpha} of Eq. (4), same indexing; method 1 selects it */
   int method;
   cplx *Mx[16];
-  /* short-range Lennard-Jones pair term (Sec. 5.4): 4 eps ((sig/r)^12 -
+  /* short-range Lennard-Jones pair term (Sec. 5.3): 4 eps ((sig/r)^12 -
    * (sig/r)^6) for r < rc, off when eps = 0 */
   double lj_eps, lj_sig, lj_rc;
   /* periodic far field: box multipole K, its conjugate E, lattice sums */
@@ -718,7 +718,7 @@ static void setup_local_fmm(orc_sys *s) {
 }
 
 /* Alg. M.3 (the multipole method's initialisation) with the K/E of
- * Sec. 3.3 (ii); the system then proposes and accepts with Alg. M.1/M.2 */
+ * Sec. 3.4 (ii); the system then proposes and accepts with Alg. M.1/M.2 */
 void orc_setup_multipole(orc_sys *s) {
   s->method = 1;
   for (int l = 2; l <= s->L; l++) {
@@ -767,7 +767,7 @@ void orc_setup_fmm(orc_sys *s) {
   s->energy = orc_energy_fresh(s);
 }
 
-/* ---- Sec. 3.3 (ii): K_n^m = sum q r^n Y_n^-m, E_n^m = sum q r^n Y_n^m ---- */
+/* ---- Sec. 3.4 (ii): K_n^m = sum q r^n Y_n^-m, E_n^m = sum q r^n Y_n^m ---- */
 static void setup_KE(orc_sys *s) {
   memset(s->K, 0, sizeof(cplx) * s->C);
   memset(s->E, 0, sizeof(cplx) * s->C);
@@ -997,7 +997,7 @@ double orc_propose(orc_sys *s, int64_t j, const double rnew[3]) {
 
   double dU_far = 0.0, dU_dip = 0.0;
   if (s->bc == ORC_BC_PBC) {
-    /* Sec. 3.3 (iv), literal: H = R(K), U = E.H, post-move dK, dE,
+    /* Sec. 3.4 (iv), literal: H = R(K), U = E.H, post-move dK, dE,
      * dH = R(dK), dU = dE.dH - U (with the factor 1/2, see far_energy) */
     double U_inf = far_energy(s, s->K, s->E);
     double c1[3], d0[3], d1[3];
@@ -1067,7 +1067,7 @@ double orc_far_delta_factored(orc_sys *s, int64_t j, const double rnew[3]) {
   return creal(a1) + 0.5 * creal(a2);
 }
 
-/* ---- Alg. L.2 with the K/E update of Sec. 3.3 (iii) ---- */
+/* ---- Alg. L.2 with the K/E update of Sec. 3.4 (iii) ---- */
 void orc_accept(orc_sys *s, int64_t j, const double rnew[3], double dE) {
   double *r = &s->pos[3 * j];
   double q = s->q[j];
@@ -1231,10 +1231,15 @@ void orc_proposal(int64_t n, double half_width, uint64_t seed, uint64_t step, ui
 }
 
 /* Metropolis-Hastings: accept iff dE <= 0 or log(u) < -beta dE.  A decision
- * within 1e-9 (relative) of the threshold is counted as borderline. */
-int64_t orc_run(orc_sys *s, int64_t n_steps, uint64_t seed, uint64_t step0, uint32_t chain,
-                double beta, double half_width, int64_t *log_j, double *log_dE,
-                uint8_t *log_acc, int64_t *n_borderline) {
+ * within 1e-9 (relative) of the threshold is counted as borderline.  With
+ * `follow` (a driver option for checking a chain whose energy changes carry
+ * a known rounding error, the paper has no counterpart), step t is accepted
+ * iff follow[t] != 0 whatever the rule says, and log_acc still records the
+ * rule's own decision. */
+static int64_t run_chain(orc_sys *s, int64_t n_steps, uint64_t seed, uint64_t step0,
+                         uint32_t chain, double beta, double half_width, const uint8_t *follow,
+                         int64_t *log_j, double *log_dE, uint8_t *log_acc,
+                         int64_t *n_borderline) {
   int64_t n_acc = 0, nb = 0;
   for (int64_t t = 0; t < n_steps; t++) {
     int64_t j;
@@ -1260,6 +1265,7 @@ int64_t orc_run(orc_sys *s, int64_t n_steps, uint64_t seed, uint64_t step0, uint
     if (log_j) log_j[t] = j;
     if (log_dE) log_dE[t] = dE;
     if (log_acc) log_acc[t] = (uint8_t)acc;
+    if (follow) acc = follow[t] != 0;
     if (acc) {
       orc_accept(s, j, rnew, dE);
       n_acc++;
@@ -1267,6 +1273,20 @@ int64_t orc_run(orc_sys *s, int64_t n_steps, uint64_t seed, uint64_t step0, uint
   }
   if (n_borderline) *n_borderline = nb;
   return n_acc;
+}
+
+int64_t orc_run(orc_sys *s, int64_t n_steps, uint64_t seed, uint64_t step0, uint32_t chain,
+                double beta, double half_width, int64_t *log_j, double *log_dE,
+                uint8_t *log_acc, int64_t *n_borderline) {
+  return run_chain(s, n_steps, seed, step0, chain, beta, half_width, NULL, log_j, log_dE, log_acc,
+                   n_borderline);
+}
+
+int64_t orc_run_follow(orc_sys *s, int64_t n_steps, uint64_t seed, uint64_t step0,
+                       uint32_t chain, double beta, double half_width, const uint8_t *follow,
+                       int64_t *log_j, double *log_dE, uint8_t *log_acc, int64_t *n_borderline) {
+  return run_chain(s, n_steps, seed, step0, chain, beta, half_width, follow, log_j, log_dE,
+                   log_acc, n_borderline);
 }
 
 /* ------------------------------------------------------------------------ */

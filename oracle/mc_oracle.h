@@ -58,12 +58,12 @@ void orc_setup_fmm(orc_sys *s);
 /* one cell's FMM-variant expansion (real layout), source multipoles taken
  * directly from the charges; -1 for a bad level */
 int orc_fmm_local_cell(orc_sys *s, int level, const int c[3], double *out);
-/* the multipole method (Sec. 3.2, alternative algorithm): Alg. M.3 + K/E +
+/* the multipole method (Sec. 3.3, alternative algorithm): Alg. M.3 + K/E +
  * U0; afterwards propose/accept/run/energy follow Alg. M.1/M.2.  orc_setup
  * or orc_setup_fmm switch back to the local method. */
 void orc_setup_multipole(orc_sys *s);
 /* short-range Lennard-Jones term 4 eps((sig/r)^12 - (sig/r)^6), r < rc
- * (Sec. 5.4; call before a setup); rc <= finest cell width, else -1 */
+ * (Sec. 5.3; call before a setup); rc <= finest cell width, else -1 */
 int orc_set_lj(orc_sys *s, double eps, double sig, double rc);
 /* level multipoles M_n^m (real layout), -1 for a bad level or before setup */
 int orc_get_multipole(const orc_sys *s, int level, double *out);
@@ -95,6 +95,13 @@ int64_t orc_run(orc_sys *s, int64_t n_steps, uint64_t seed, uint64_t step0,
                 uint32_t chain, double beta, double half_width,
                 int64_t *log_j, double *log_dE, uint8_t *log_acc,
                 int64_t *n_borderline);
+/* as orc_run, but step t is accepted iff follow[t] != 0 (log_acc keeps the
+ * rule's own decision): replays the states of a chain whose decisions were
+ * taken elsewhere */
+int64_t orc_run_follow(orc_sys *s, int64_t n_steps, uint64_t seed, uint64_t step0,
+                       uint32_t chain, double beta, double half_width, const uint8_t *follow,
+                       int64_t *log_j, double *log_dE, uint8_t *log_acc,
+                       int64_t *n_borderline);
 
 /* ---- exact periodic Coulomb energy by Ewald summation (tinfoil) ---- */
 double orc_ewald_energy(int64_t n, const double *pos, const double *q, double a,

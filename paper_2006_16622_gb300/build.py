@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libmcfmm.so")
-SOURCES = ["mc_capi.cu", "mc_chain.cu", "mc_pipe.cu", "mc_setup.cu", "mc_noalloc.cu", "mc_async.cu"]
+SOURCES = ["mc_capi.cu", "mc_chain.cu", "mc_setup.cu", "mc_noalloc.cu", "mc_async.cu", "mc_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-D__NV_NO_VECTOR_DEPRECATION_DIAG", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-O2"]

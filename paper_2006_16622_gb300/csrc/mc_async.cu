@@ -1,5 +1,5 @@
 // Asynchronous persistent chain kernel (MC_SCHEDULE_ASYNC): the steps of
-// Alg. L.1 (propose, with Alg. 1 and the periodic terms of Sec. 3.3) and
+// Alg. L.1 (propose, with Alg. 1 and the periodic terms of Sec. 3.4) and
 // Alg. L.2 (accept, its contributions computed speculatively) for one
 // system, with no grid or CTA barrier inside the step loop.  Warps meet
 // only through data:
@@ -791,7 +791,7 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
           double partial = 0.0;
           int ptype = 3;
           if (it < iN) {
-            // ---- F: far lattice, Sec. 3.3 (iv) in the factored form
+            // ---- F: far lattice, Sec. 3.4 (iv) in the factored form
             //   dU_inf = sum_k W_k dK_k (H_k + 1/2 (G dK)_k),  W = 1 (m = 0) or 2
             ptype = 2;
             const int f = it;
@@ -874,7 +874,7 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
               }
             }
           } else if (it == iX) {
-            // ---- X: periodic self-interaction correction (Sec. 3.3, last
+            // ---- X: periodic self-interaction correction (Sec. 3.4, last
             //      item) and the dipole term (tinfoil reading); +inf when r'
             //      left a free-space box
             if (g.outside) {

@@ -19,19 +19,13 @@
 // kernels defined in the other translation units
 cudaError_t mc_launch_chain(const McSys* d_sys, const RunParams& rp, int prec, int var, int nCTA,
                             cudaStream_t stream);
-cudaError_t mc_launch_pipe(const McSys* d_sys, const RunParams& rp, int prec, int nCTA,
-                           cudaStream_t stream);
 cudaError_t mc_launch_async(const McSys* d_sys, const RunParams& rp, int prec, int nCTA,
                             cudaStream_t stream);
-cudaError_t mc_launch_batch_pipe(const McSys* const* d_systems, RunParams* d_rps,
-                                 const int* d_cta_chain, const int* d_cta_rank,
-                                 const int* d_chain_ctas, int prec, int nCTA, cudaStream_t stream);
 cudaError_t mc_launch_batch(const McSys* const* d_systems, RunParams* d_rps, const int* d_cta_chain,
                             const int* d_cta_rank, const int* d_chain_ctas, int prec, int var,
                             int nCTA, cudaStream_t stream);
 int mc_chain_max_ctas(int prec);
 int mc_batch_max_ctas(int prec);
-int mc_batch_pipe_ctas_per_sm(int prec);
 __global__ void k_cell_count(int, const double4*, double, int, int*, int*);
 __global__ void k_cell_fill(int, const int*, int, int*, int*);
 __global__ void k_cell_sort(int, int, int, double, const int*, const double4*, int*, double4*,
@@ -136,11 +130,9 @@ int launch_chain(mc_ctx* c, RunParams& rp) {
   rp.bar_missing = c->bar_missing;
   rp.prof = c->d_prof;
   const bool mm = c->h.method == 1;
-  // the pipelined kernel has no Lennard-Jones term: phased instead
-  const bool piped = !mm && !c->h.lj_on && rp.mode == 0 && c->schedule == MC_SCHEDULE_PIPELINED;
   // single proposals and the multipole method run on the phased kernel
   const bool async = !mm && rp.mode == 0 && c->schedule == MC_SCHEDULE_ASYNC;
-  rp.nf_cols = piped ? 4 : MC_NF_COLS;
+  rp.nf_cols = MC_NF_COLS;
   rp.spec = (!mm && (c->schedule == MC_SCHEDULE_PHASED || c->schedule == MC_SCHEDULE_ASYNC)) ? 1 : 0;
   rp.chain = 0u;
   // grid: the caller's (mc_set_ctas), else every SM, except for the phased
@@ -151,7 +143,7 @@ int launch_chain(mc_ctx* c, RunParams& rp) {
   // warps: -4 % on 128 CTAs, -15 % on 114 at N = 1e5)
   int grid = c->nCTA;
   if (grid == 0)
-    grid = (!mm && !async && !piped && rp.spec && c->h.prec == MC_FP32_EVAL) ? std::max(1, (5 * c->sms) / 7) : c->sms;
+    grid = (!mm && !async && rp.spec && c->h.prec == MC_FP32_EVAL) ? std::max(1, (5 * c->sms) / 7) : c->sms;
   CK(cudaMemsetAsync(c->h.bar, 0, sizeof(unsigned long long), c->stream));
   CK(cudaMemsetAsync(c->h.status, 0, sizeof(int), c->stream));
   if (async) {
@@ -162,11 +154,6 @@ int launch_chain(mc_ctx* c, RunParams& rp) {
     if (c->h.nsmall > 0)
       CK(cudaMemsetAsync(c->h.dsmall, 0, sizeof(double) * 4 * (size_t)c->h.nsmall * c->h.C, c->stream));
     CK(mc_launch_async(c->d_sys, rp, c->h.prec, grid, c->stream));
-  } else if (piped) {
-    // accept of step k overlaps the proposal of k+1
-    CK(cudaMemsetAsync(c->h.sync, 0, sizeof(unsigned long long) * 16, c->stream));
-    CK(cudaMemsetAsync(c->h.dsmall, 0, sizeof(double) * 3 * (size_t)c->h.nsmall * c->h.C, c->stream));
-    CK(mc_launch_pipe(c->d_sys, rp, c->h.prec, grid, c->stream));
   } else {
     // the two small-level delta buffers of the speculative accept start clear
     if (rp.spec && c->h.nsmall > 0)
@@ -350,6 +337,7 @@ const char* mc_strerror(int s) {
     case MC_ERR_STATE: return "call out of order";
     case MC_ERR_NOMEM: return "device allocation failed";
     case MC_ERR_SCRATCH: return "request exceeds the fixed no-allocation scratch";
+    case MC_ERR_PENDING: return "a CUDA error of earlier work was pending";
     default: return "unknown status";
   }
 }
@@ -487,8 +475,6 @@ int mc_init(mc_ctx** out, int64_t n, const double* pos, const double* q, double 
     }
   h.nsmall = h.lev_off[h.ls_end > h.L ? h.L : h.ls_end] + (h.ls_end > h.L ? h.lev_n[h.L] * h.lev_n[h.L] * h.lev_n[h.L] : 0);
   if (h.ls_end <= h.lmin) h.nsmall = 0;
-  DA(h.Hhat2, sizeof(double) * C);
-  DA(h.dipv2, sizeof(double) * 3);
   DA(h.dsmall, sizeof(double) * 4 * (size_t)std::max(1, h.nsmall) * C);
   DA(h.sync, sizeof(unsigned long long) * 128);
   DA(h.dacc, sizeof(double) * 8 * (size_t)(levels - h.lmin + 1) * MC_DSLOTS * C);
@@ -674,6 +660,8 @@ int mc_run(mc_ctx* c, int64_t n_steps, uint64_t seed, double beta, double half_w
         break;
       }
       st.max_drift = std::max(st.max_drift, fabs(run_e - fresh));
+      st.sum_drift += run_e - fresh;
+      st.sum_abs_drift += fabs(run_e - fresh);
       st.resetups++;
       if (cudaMemcpy(c->h.energy, &fresh, sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
         rc = MC_ERR_CUDA;
@@ -700,6 +688,12 @@ int mc_run(mc_ctx* c, int64_t n_steps, uint64_t seed, double beta, double half_w
     *stats = st;
   }
   return rc;
+}
+
+int mc_step_counter(mc_ctx* c, int64_t* out) {
+  if (!c || !out) return MC_ERR_ARG;
+  *out = (int64_t)c->steps_total;
+  return MC_OK;
 }
 
 int mc_energy(mc_ctx* c, double* e) {
@@ -850,8 +844,8 @@ int mc_profile_read(mc_ctx* c, uint64_t* out) {
 }
 
 int mc_set_schedule(mc_ctx* c, int schedule) {
-  if (!c || (schedule != MC_SCHEDULE_PHASED && schedule != MC_SCHEDULE_PIPELINED &&
-             schedule != MC_SCHEDULE_PLAIN && schedule != MC_SCHEDULE_ASYNC))
+  if (!c || (schedule != MC_SCHEDULE_PHASED && schedule != MC_SCHEDULE_PLAIN &&
+             schedule != MC_SCHEDULE_ASYNC))
     return MC_ERR_ARG;
   c->schedule = schedule;
   return MC_OK;
@@ -988,12 +982,7 @@ int batch_enqueue(mc_batch* b) {
     CK(cudaMemsetAsync(b->ctxs[i]->h.dsmall, 0,
                        sizeof(double) * 3 * (size_t)b->ctxs[i]->h.nsmall * b->ctxs[i]->h.C, b->stream));
   }
-  bool any_lj = false;
-  for (int i = 0; i < b->n; i++) any_lj = any_lj || b->ctxs[i]->h.lj_on;
-  if (b->schedule == MC_SCHEDULE_PIPELINED && b->ctxs[0]->h.method == 0 && !any_lj) {
-    CK(mc_launch_batch_pipe(b->d_systems, b->d_rps, b->d_cta_chain, b->d_cta_rank,
-                            b->d_chain_ctas, b->prec, b->nCTA, b->stream));
-  } else {
+  {
     // phased FP64: the column-scaled contributions (fewer FP64 instructions
     // for this throughput-bound form)
     const int var = b->ctxs[0]->h.method == 1 ? MC_VAR_MM
@@ -1054,10 +1043,8 @@ int mc_batch_create(mc_batch** out, int n_chains, mc_ctx* const* ctxs) {
     return MC_ERR_CUDA;
   }
   {
-    // the batch's CTAs: its kernels' occupancy (pipelined kernel included)
-    int dev_sms = 0;
-    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, b->dev);
-    b->sms = std::min(mc_batch_max_ctas(b->prec), dev_sms * mc_batch_pipe_ctas_per_sm(b->prec));
+    // the batch's CTAs: its kernels' occupancy
+    b->sms = mc_batch_max_ctas(b->prec);
   }
   if (b->sms < 1) {
     delete b;
@@ -1118,8 +1105,7 @@ void mc_batch_destroy(mc_batch* b) {
 }
 
 int mc_batch_set_schedule(mc_batch* b, int schedule) {
-  if (!b || (schedule != MC_SCHEDULE_PHASED && schedule != MC_SCHEDULE_PIPELINED &&
-             schedule != MC_SCHEDULE_PLAIN))
+  if (!b || (schedule != MC_SCHEDULE_PHASED && schedule != MC_SCHEDULE_PLAIN))
     return MC_ERR_ARG;
   b->schedule = schedule;
   if (b->g_valid) {

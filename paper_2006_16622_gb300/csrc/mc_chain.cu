@@ -1,6 +1,6 @@
 // Persistent Metropolis-Hastings chain kernel: one cooperative launch runs
 // many steps of Alg. L.1 (propose, with Alg. 1 and the periodic terms of
-// Sec. 3.3) and Alg. L.2 (accept) for one system on the whole GPU.
+// Sec. 3.4) and Alg. L.2 (accept) for one system on the whole GPU.
 //
 // One step:
 //   1. warp 0 of every CTA draws the same Philox proposal (j, r -> r') and
@@ -592,7 +592,7 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
         const TE accn = __shfl_sync(0xffffffffu, acc, 8);
         partial = g.q * to_double(accn - acc);
       } else if (it < iE) {
-        // ---- F: far lattice, Sec. 3.3 (iv) in the factored form
+        // ---- F: far lattice, Sec. 3.4 (iv) in the factored form
         //   dU_inf = sum_k W_k dK_k (H_k + 1/2 (G dK)_k),  W = 1 (m = 0) or 2
         ptype = 2;
         const int f = it - iF;
@@ -656,7 +656,7 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
                       },
                       &partial);
       } else if (it == iX) {
-        // ---- X: periodic self-interaction correction (Sec. 3.3, last item)
+        // ---- X: periodic self-interaction correction (Sec. 3.4, last item)
         //         and the dipole term (tinfoil reading)
         ptype = 3;
         item_image<TE>(S, g, pbc, lane,

@@ -70,10 +70,7 @@ struct McSys {
   int* status;       // device status word (MC_OK or MC_ERR_*)
   long long* stats;  // [4] steps, accepted, borderline, spare
   double* result;    // [4] dE of a single proposal, ...
-  // pipelined chain (mc_pipe.cu): second H and dipole buffers, speculative
-  // coarse-level deltas (3 rotating buffers of nsmall cells x C), sync words
-  double* Hhat2;     // [C]
-  double* dipv2;     // [3]
+  // speculative small-level deltas (rotating buffers of nsmall cells x C)
   double* dsmall;    // [4 * nsmall * C] (rotating buffers: three or four)
   int ls_end;        // first level with more than 4 cells per axis (or L + 1)
   int nsmall;        // cells of levels lmin .. ls_end-1 (the first cells of Lhat)
@@ -83,11 +80,11 @@ struct McSys {
   double* dacc;      // [4 (step) * (L - lmin + 1) * 2 * MC_DSLOTS * C] (phased: by step parity;
                      // mc_async.cu: by step mod 4 and side)
   double* dKpre;     // [4 * C] dK of the next proposal, by step (2 or 4 buffers)
-  // multipole method (Sec. 3.2, alternative algorithm; method 1): per-level
+  // multipole method (Sec. 3.3, alternative algorithm; method 1): per-level
   // scaled multipoles Mhat_n^m = sum q conj Rt_n^m(r - R_cell), Lhat's layout
   int method;
   double* Mhat;
-  // short-range Lennard-Jones term (Sec. 5.4): 4 eps ((sig/r)^12 - (sig/r)^6)
+  // short-range Lennard-Jones term (Sec. 5.3): 4 eps ((sig/r)^12 - (sig/r)^6)
   // for r^2 < rc2, between different particles of the near cells
   int lj_on;
   double lj_eps4, lj_s6, lj_s12, lj_rc2;

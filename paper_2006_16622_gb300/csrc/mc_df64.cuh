@@ -147,13 +147,18 @@ __device__ __forceinline__ double f2d_int(float f) {
   const uint32_t lo = e ? (b << 29) : 0u;
   return __hiloint2double((int)hi, (int)lo);
 }
-// double -> float rounded toward zero; |x| beyond the float range saturates
-// to +-inf, below it flushes to 0 (branch-free).
+// double -> float rounded to nearest (ties to even), as the IEEE
+// conversion; a result beyond the float range saturates to +-inf, an input
+// below the smallest normal float flushes to 0 (branch-free).  The 29
+// dropped significand bits decide the rounding; a carry out of the
+// significand moves into the exponent, as IEEE rounding does.
 __device__ __forceinline__ float d2f_int(double x) {
   const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
   const int e = (int)((hi >> 20) & 0x7ffu) - 896;
   uint32_t mag = ((uint32_t)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const uint32_t rem = lo & 0x1fffffffu, half = 0x10000000u;
+  mag += (rem > half || (rem == half && (mag & 1u))) ? 1u : 0u;
   mag = (e <= 0) ? 0u : mag;
-  mag = (e >= 255) ? 0x7f800000u : mag;
+  mag = (e >= 255 || mag > 0x7f800000u) ? 0x7f800000u : mag;
   return __uint_as_float((hi & 0x80000000u) | mag);
 }

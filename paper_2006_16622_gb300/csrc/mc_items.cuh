@@ -131,28 +131,66 @@ __device__ __forceinline__ bool item_near(const McSys& S, const StepGeo& g,
       const float qf = d2f_int(g.q);
       const float e4 = d2f_int(S.lj_eps4), s6 = d2f_int(S.lj_s6), s12 = d2f_int(S.lj_s12),
                   rc2 = d2f_int(S.lj_rc2);
+      // close pairs: the FP32 cell-relative coordinates carry an absolute
+      // error of ~1e-7 w (w the finest cell width), which a pair at distance
+      // d turns into ~1e-7 w / d^2 of energy; pairs closer than w/8 are
+      // therefore summed in FP64 from the absolute positions (rare: ~0.4 per
+      // step at 24 charges per cell), which bounds the FP32 pair error by
+      // ~1e-5 w^-1, and an exact overlap is decided in FP64 as in the FP64 form
+      const float close2 = d2f_int(wL * wL * (1.0 / 64.0));
+      double acc64 = 0.0;
+      bool any_close = false;
       for (int s = lane; s < cnt; s += 32) {
         const float4 xi = __ldcg(&S.cpos32[(size_t)cell * S.cap + s]);
         const int pid = (side != 1 || lj) ? __ldcg(&S.cpid[(size_t)cell * S.cap + s]) : -1;
+        bool close_o = false, close_n = false;
         if (side != 1) {
           if (!(pid == g.j && zero_shift)) {
             const float ax = ox - xi.x, ay = oy - xi.y, az = oz - xi.z;
             const float d2 = ax * ax + ay * ay + az * az;
-            const float ir = rsqrtf(d2);
-            acc -= qf * xi.w * ir;
-            if (lj && pid != g.j) acc -= lj_energy(ir * ir, d2, e4, s6, s12, rc2);
+            if (d2 < close2) {
+              close_o = true;
+            } else {
+              const float ir = rsqrtf(d2);
+              acc -= qf * xi.w * ir;
+              if (lj && pid != g.j) acc -= lj_energy(ir * ir, d2, e4, s6, s12, rc2);
+            }
           }
         }
         if (side != 0) {
           const float bx = nx - xi.x, by = ny - xi.y, bz = nz - xi.z;
           const float d2 = bx * bx + by * by + bz * bz;
-          if (d2 == 0.0f) ovl = true;
-          const float ir = rsqrtf(d2);
-          acc += qf * xi.w * ir;
-          if (lj && pid != g.j) acc += lj_energy(ir * ir, d2, e4, s6, s12, rc2);
+          if (d2 < close2) {
+            close_n = true;
+          } else {
+            const float ir = rsqrtf(d2);
+            acc += qf * xi.w * ir;
+            if (lj && pid != g.j) acc += lj_energy(ir * ir, d2, e4, s6, s12, rc2);
+          }
+        }
+        if (close_o || close_n) {
+          any_close = true;
+          const double4 x64 = ldcg4(&S.cpos[(size_t)cell * S.cap + s]);
+          const double sx = s0 * S.a, sy = s1 * S.a, sz = s2 * S.a;
+          if (close_o) {
+            const double ax = (g.r[0] - sx) - x64.x, ay = (g.r[1] - sy) - x64.y, az = (g.r[2] - sz) - x64.z;
+            const double d2 = ax * ax + ay * ay + az * az;
+            const double ir = rsqrt(d2);
+            acc64 -= g.q * x64.w * ir;
+            if (lj && pid != g.j) acc64 -= lj_energy(ir * ir, d2, S.lj_eps4, S.lj_s6, S.lj_s12, S.lj_rc2);
+          }
+          if (close_n) {
+            const double bx = (g.rn[0] - sx) - x64.x, by = (g.rn[1] - sy) - x64.y, bz = (g.rn[2] - sz) - x64.z;
+            const double d2 = bx * bx + by * by + bz * bz;
+            if (d2 == 0.0) ovl = true;
+            const double ir = rsqrt(d2);
+            acc64 += g.q * x64.w * ir;
+            if (lj && pid != g.j) acc64 += lj_energy(ir * ir, d2, S.lj_eps4, S.lj_s6, S.lj_s12, S.lj_rc2);
+          }
         }
       }
       partial = f2d_int(warp_sum(acc));
+      if (__any_sync(0xffffffffu, any_close)) partial += warp_sum(acc64);
     }
     if (__any_sync(0xffffffffu, ovl)) partial = kInf;
   }
@@ -160,7 +198,7 @@ __device__ __forceinline__ bool item_near(const McSys& S, const StepGeo& g,
   return true;
 }
 
-// Periodic self-interaction correction (Sec. 3.3, last item: the moving
+// Periodic self-interaction correction (Sec. 3.4, last item: the moving
 // charge's images) and, with tinfoil boundary conditions, the dipole term;
 // free space: the charge's interaction with its old position.  wait() is
 // called before the dipole sum is read.

@@ -1,5 +1,5 @@
-// Allocation-free entry point: the local expansions of one level (the
-// gather form of Alg. L.3) computed from caller-owned device buffers, with
+// Allocation-free entry point: the local expansions of one level (computed
+// as the gather form of Alg. L.3 that mc_setup uses) from caller-owned device buffers, with
 // the per-chunk partial expansions kept in a fixed device array that this
 // file owns.  It exists for callers that must not have the library call
 // cudaMalloc or cudaFree: code that manages every byte of device memory
@@ -132,7 +132,9 @@ __global__ void k_reduce_noalloc(int ntarget, int nchunk, int C, const double* _
   }
 }
 
-// device address of the scratch, looked up once per device
+// device address of the scratch, looked up once per device and kept for the
+// life of the process (a cudaDeviceReset would make it stale; the header
+// forbids calls after one)
 constexpr int kMaxDevices = 64;
 double* g_scratch_ptr[kMaxDevices];
 std::mutex g_scratch_mutex;
@@ -144,7 +146,7 @@ int scratch_for_current_device(double** out) {
   if (!g_scratch_ptr[dev]) {
     void* ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
-      cudaGetLastError();
+      cudaGetLastError();  // the failed lookup's own error (none was pending)
       return MC_ERR_CUDA;
     }
     g_scratch_ptr[dev] = (double*)ptr;
@@ -176,6 +178,9 @@ extern "C" int mc_p2l_level_noalloc(const double* d_part, const int* d_cell_star
   long long nchunk = (4LL * sms * MC_WARPS + ncl - 1) / ncl;
   nchunk = nchunk < 1 ? 1 : (nchunk > 189 ? 189 : nchunk);
   while (nchunk > 1 && ncl * nchunk * C > (long long)MC_NOALLOC_SCRATCH_DOUBLES) nchunk--;
+  // an error left by the caller's earlier work is not ours to clear or
+  // report as this call's own: launch nothing
+  if (cudaPeekAtLastError() != cudaSuccess) return MC_ERR_PENDING;
   double* scratch = nullptr;
   int rc = scratch_for_current_device(&scratch);
   if (rc != MC_OK) return rc;
@@ -194,6 +199,7 @@ extern "C" int mc_p2l_level_noalloc(const double* d_part, const int* d_cell_star
   long long blocks = (ntask + MC_WARPS - 1) / MC_WARPS;
   if (blocks > 8LL * sms) blocks = 8LL * sms;
   k_p2l_level_noalloc<<<(int)blocks, MC_THREADS, 0, stream>>>(P, d_part, d_cell_start, scratch);
+  // no error was pending before the launch, so one now is the launch's own
   if (cudaGetLastError() != cudaSuccess) return MC_ERR_CUDA;
   long long rb = (ncl * C + 255) / 256;
   if (rb > 8LL * sms) rb = 8LL * sms;

@@ -1,6 +1,6 @@
 // Setup-side kernels: cell lists, Alg. L.3 (initialise the level local
 // expansions) as a per-target gather, the box multipole K and lattice local
-// expansion H = R(K) of Sec. 3.3 (ii)/(iv), the total energy, and the lattice
+// expansion H = R(K) of Sec. 3.4 (ii)/(iv), the total energy, and the lattice
 // sums / far-field operator behind R.  All FP64.
 #include <math.h>
 
@@ -178,7 +178,7 @@ __global__ void k_reduce_chunks(int ntarget, int nchunk, int C, const double* __
   }
 }
 
-// ------------------------------------------- K (Sec. 3.3 ii) and the dipole
+// ------------------------------------------- K (Sec. 3.4 ii) and the dipole
 // chunk ch of the particles: partial Khat = sum q conj Rt(r - R1); dipole
 // sum q r appended at [C .. C+2].
 __global__ void __launch_bounds__(MC_THREADS)

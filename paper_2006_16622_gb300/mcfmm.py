@@ -28,13 +28,14 @@ EXPORTED = ["mc_init", "mc_setup", "mc_propose", "mc_accept", "mc_run", "mc_ener
             "mc_destroy", "mc_strerror", "mc_p2l_level_noalloc", "mc_batch_create",
             "mc_batch_tune", "mc_batch_run", "mc_batch_info", "mc_batch_destroy",
             "mc_set_schedule", "mc_set_ctas", "mc_batch_set_schedule", "mc_inject_wait_fault",
-            "mc_get_multipole", "mc_set_lj"]
+            "mc_get_multipole", "mc_set_lj", "mc_step_counter", "mc_probe_fma_rate"]
 
 
 class McStats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("accepted", ctypes.c_int64),
                 ("borderline", ctypes.c_int64), ("resetups", ctypes.c_int64),
-                ("energy", ctypes.c_double), ("max_drift", ctypes.c_double)]
+                ("energy", ctypes.c_double), ("max_drift", ctypes.c_double),
+                ("sum_drift", ctypes.c_double), ("sum_abs_drift", ctypes.c_double)]
 
 
 class McError(RuntimeError):
@@ -61,6 +62,8 @@ def load(path: str = LIB_PATH):
     L.mc_accept.argtypes = [P, I64, P, P]
     L.mc_run.argtypes = [P, I64, U64, D, D, I64, P, P, P, P]
     L.mc_energy.argtypes = [P, P]
+    L.mc_step_counter.argtypes = [P, P]
+    L.mc_probe_fma_rate.argtypes = [I, D, P]
     L.mc_energy_fresh.argtypes = [P, P]
     L.mc_get_positions.argtypes = [P, P]
     L.mc_get_local.argtypes = [P, I, P]
@@ -117,6 +120,14 @@ def p2l_level_noalloc(d_part, d_cell_start, n, box, levels, level, p, bc, d_out,
                                        int(n), float(box), int(levels), int(level), int(p),
                                        int(bc), ctypes.c_void_p(d_out),
                                        ctypes.c_void_p(stream) if stream else None)
+
+
+def probe_fma_rate(fp64: bool, target_seconds: float = 0.2) -> float:
+    """Measured FMA-pipe peak of the current device in flop/s (FP64 or FP32)."""
+    out = np.zeros(1)
+    _check(load().mc_probe_fma_rate(1 if fp64 else 0, float(target_seconds), _ptr(out)),
+           "mc_probe_fma_rate")
+    return float(out[0])
 
 
 def lattice_sums(lmax: int):
@@ -185,6 +196,11 @@ class Context:
         out = np.zeros(1)
         _check(load().mc_energy(self._h, _ptr(out)), "mc_energy")
         return float(out[0])
+
+    def step_counter(self):
+        out = np.zeros(1, dtype=np.int64)
+        _check(load().mc_step_counter(self._h, _ptr(out)), "mc_step_counter")
+        return int(out[0])
 
     def energy_fresh(self):
         out = np.zeros(1)

@@ -128,7 +128,7 @@ def study_moves(n: int, a: float, pos, count: int, seed: int, half_width: float 
     return js, rn
 
 
-# Full Monte Carlo NaCl runs (Sec. 5.4): the paper adds a repulsive
+# Full Monte Carlo NaCl runs (Sec. 5.3): the paper adds a repulsive
 # Lennard-Jones term with a 12 Angstrom cutoff and gives no parameters;
 # reading: epsilon = 0.1 eV (in e^2/Angstrom) and sigma with the well
 # minimum at the lattice spacing.  Largest crystal: 46^3 ions in a 153.2

@@ -54,3 +54,42 @@ def test_roofline_step_times(bench):
     assert t32 < t64
     bw, _ = bench.hbm_peak_bytes()
     assert t32 == pytest.approx(bench.bytes_per_step(12, 5, nbar, 0.9) / bw)  # FP32-eval: the HBM term
+
+
+def test_result_line_fits_the_stored_tail(bench):
+    """The result line keeps every form and its roofline fraction within the
+    last 1500 characters of the output (the bulky legs go on the line before)."""
+    import json
+
+    class A:
+        steps, warmup, mh_steps = 20, 5, 50_000
+    r64 = {"clocks": {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 599}}
+    e2e = {"value": 61870.47288800432, "unit": "MH steps/s", "h2d_bytes_per_step": 3200000,
+           "d2h_bytes_per_step": 3200008,
+           "what": "mc_init from host arrays, mc_setup, mc_run, positions+energy back, mc_destroy"}
+    roof = {"bound": "alu", "achieved": 0.11386945026033803, "peak": 1.25856, "unit": "TFLOP/s",
+            "frac": 0.09047598069248826, "traffic": 82680000.0,
+            "traffic_source": "ncu summary of one full launch (profiles/), null if taken on other sources",
+            "kernel": "mc_async_kernel<double>",
+            "peak_source": "derived",
+            "peak_measured": 1.2012345678, "frac_of_measured": 0.0951234567,
+            "flops_per_mh_step": 1325465.733925, "acceptance": 0.8496}
+    cpu = bench.cpu_baseline_from({"value": 1171.5416817472792, "sample": 3000, "setup_s": 41.2})
+    forms = {"fp64": 85909.0109580918, "fp32_eval": 88831.123456, "multipole_fp64": 56468.123456,
+             "batched_fp64": 558506.123456, "batched_fp32_eval": 911236.123456,
+             "n1e6_fp64": 73544.123456, "n1e6_fp32_eval": 84665.123456}
+    fr = {"fp64": 0.0951234567, "fp32_eval": 0.0281234567, "batched_fp32_eval": 0.151234567,
+          "batched_fp64": 0.321234567}
+    prec = {"moves": 10_000_000, "dE_err_p95": 5.7e-06, "dE_err_max": 0.00014,
+            "fp32_eval": {"mh_steps_per_s": 80123.456, "resetups": 89,
+                          "drift_mean_abs_per_1e6_acc": 0.19812345},
+            "fp64_floor": {"drift_mean_abs_per_1e6_acc": 0.0028123}}
+    line = bench.compact_line(85909.0109580918, 582.0111236572266, A, 1, r64, e2e, roof, cpu,
+                              forms, fr, prec, "uniform N=100000 rho=0.1 a=100 L=5 p=12 h=0.3")
+    text = json.dumps(line)
+    assert len(text) < 1450, len(text)
+    back = json.loads(text)
+    for k in ("fp64", "fp32_eval", "batched_fp64", "batched_fp32_eval"):
+        assert k in back["forms"] and k in back["roofline_frac"]
+    for k in ("metric", "value", "unit", "roofline", "cpu_baseline", "e2e", "clocks", "gpu_launches"):
+        assert k in back

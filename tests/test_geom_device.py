@@ -2,7 +2,7 @@
 
 The device header is compiled for the host with g++ and compared with the
 oracle's interaction lists (Sec. 3.1, with the periodic images of
-Sec. 3.3), cell by cell:
+Sec. 3.4), cell by cell:
 
   - the per-parity offset table holds the 189 offsets of every cell's list;
   - on levels with at most 4 cells per axis, the 189 accept entries of a

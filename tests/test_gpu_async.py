@@ -63,6 +63,8 @@ def test_default_schedule_by_precision():
         assert (pr[2] == 0) == async_default, pr[:8]
         with pytest.raises(mcfmm.McError):
             g.set_schedule(7)
+        with pytest.raises(mcfmm.McError):  # the withdrawn pipelined schedule
+            g.set_schedule(mcfmm.SCHEDULE_PIPELINED)
         g.close()
 
 

@@ -39,7 +39,6 @@ def _lib():
 
 
 @pytest.mark.parametrize("precision,schedule", [(mcfmm.FP64, mcfmm.SCHEDULE_PHASED),
-                                                (mcfmm.FP64, mcfmm.SCHEDULE_PIPELINED),
                                                 (mcfmm.FP64, mcfmm.SCHEDULE_PLAIN)])
 def test_batch_replays_every_chain(precision, schedule):
     syst = _systems()

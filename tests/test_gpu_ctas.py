@@ -41,7 +41,7 @@ def system():
 
 
 @pytest.mark.parametrize("schedule", [mcfmm.SCHEDULE_ASYNC, mcfmm.SCHEDULE_PHASED,
-                                      mcfmm.SCHEDULE_PLAIN, mcfmm.SCHEDULE_PIPELINED])
+                                      mcfmm.SCHEDULE_PLAIN])
 @pytest.mark.parametrize("n_cta", [3, 37, 100])
 def test_small_grid_replays_oracle(system, schedule, n_cta):
     pos, q, a, L, p, ro = system

@@ -1,4 +1,4 @@
-"""The short-range Lennard-Jones term (Sec. 5.4) on the GPU against the oracle.
+"""The short-range Lennard-Jones term (Sec. 5.3) on the GPU against the oracle.
 
 A perturbed 8^3 NaCl crystal (spacing 3.3 A, 2 levels: finest cells of
 13.2 A hold every pair within the 12 A cutoff) at T = 273 K with moves of

@@ -93,8 +93,8 @@ def test_propose_accept_sequence(bc):
     assert _rel(g.energy(), o.energy()) <= DE_TOL
 
 
-@pytest.mark.parametrize("schedule", [mcfmm.SCHEDULE_PHASED, mcfmm.SCHEDULE_PIPELINED,
-                                      mcfmm.SCHEDULE_PLAIN, mcfmm.SCHEDULE_ASYNC])
+@pytest.mark.parametrize("schedule", [mcfmm.SCHEDULE_PHASED, mcfmm.SCHEDULE_PLAIN,
+                                      mcfmm.SCHEDULE_ASYNC])
 def test_replay_small_workload_full_chain(schedule):
     """N=1000, a=10, L=3, p=8, h=0.5, beta=1, seed 0: the full 10^4-move chain"""
     n, a, L, p = 1000, 10.0, 3, 8
@@ -113,8 +113,8 @@ def test_replay_small_workload_full_chain(schedule):
     assert np.array_equal(g.positions(), o.positions())
 
 
-@pytest.mark.parametrize("schedule", [mcfmm.SCHEDULE_PHASED, mcfmm.SCHEDULE_PIPELINED,
-                                      mcfmm.SCHEDULE_PLAIN, mcfmm.SCHEDULE_ASYNC])
+@pytest.mark.parametrize("schedule", [mcfmm.SCHEDULE_PHASED, mcfmm.SCHEDULE_PLAIN,
+                                      mcfmm.SCHEDULE_ASYNC])
 def test_replay_ragged_and_edge_cases(schedule):
     # tiny box with 2 cells per axis (27 image copies of every cell), p = 0
     for (n, a, L, p) in [(16, 3.0, 2, 0), (40, 5.0, 2, 3), (126, 7.0, 3, 5), (900, 9.0, 4, 7)]:

@@ -251,7 +251,7 @@ def test_propose_matches_ewald_difference():
         pos2[j] = rn
         dEx = O.ewald_energy(pos2, q, a) - O.ewald_energy(pos, q, a)
         assert abs(dE - dEx) < 1e-6 * max(1.0, abs(dEx))
-        # factored far field equals the literal form of Sec. 3.3 (iv)
+        # factored far field equals the literal form of Sec. 3.4 (iv)
         lit = s.last_parts()[2]
         assert abs(s.far_delta_factored(j, rn) - lit) < 1e-13 * max(1.0, abs(lit))
         if t % 2 == 0:
@@ -362,6 +362,34 @@ def test_metropolis_rule_limits():
     s2.setup()
     r2 = s2.run(200, seed=1, beta=1e12, half_width=0.3)
     assert np.array_equal(r2["acc"].astype(bool), r2["dE"] <= 0)
+
+
+def test_follow_driver_reproduces_the_chain_and_a_frozen_system():
+    """The driver option that takes another chain's decisions: following the
+    chain's own decisions gives the chain itself; following "reject all"
+    leaves the system as it was, so every dE is a proposal on the initial
+    state (Alg. L.1 evaluated directly) and the positions do not move."""
+    pos, q = uniform_system(120, 6.0, seed=8)
+    a = O.System(pos, q, 6.0, 3, 5)
+    a.setup()
+    ra = a.run(300, seed=4, step0=10, chain=2, beta=1.0, half_width=0.5)
+    b = O.System(pos, q, 6.0, 3, 5)
+    b.setup()
+    rb = b.run_follow(ra["acc"], seed=4, step0=10, chain=2, beta=1.0, half_width=0.5)
+    assert np.array_equal(ra["j"], rb["j"]) and np.array_equal(ra["acc"], rb["acc"])
+    assert np.array_equal(ra["dE"], rb["dE"]) and ra["n_acc"] == rb["n_acc"]
+    assert np.array_equal(a.positions(), b.positions())
+    c = O.System(pos, q, 6.0, 3, 5)
+    c.setup()
+    rc = c.run_follow(np.zeros(40, np.uint8), seed=4, step0=10, chain=2, beta=1.0, half_width=0.5)
+    assert rc["n_acc"] == 0 and np.array_equal(c.positions(), pos)
+    d = O.System(pos, q, 6.0, 3, 5)
+    d.setup()
+    for t in range(40):
+        j, dl, _ = O.proposal(120, 0.5, 4, 10 + t, 2)
+        rn = (pos[j] + dl) % 6.0
+        assert rc["j"][t] == j
+        assert rc["dE"][t] == d.propose(j, rn)
 
 
 def test_proposal_stream_statistics():
@@ -524,7 +552,7 @@ def _lj_brute(pos, a, eps, sig, rc, skip=None):
 
 
 def test_lennard_jones_energy_and_moves_match_pair_sums():
-    """The LJ term of Sec. 5.4 (cutoff no larger than the finest cell, so
+    """The LJ term of Sec. 5.3 (cutoff no larger than the finest cell, so
     the 27 near cells hold every pair in range): energy and dE equal direct
     minimum-image pair sums; the moving particle's old copy is excluded."""
     a, L, rc, eps, sig = 24.0, 2, 12.0, 0.02, 1.1

@@ -304,10 +304,15 @@ int main() {
       const double want = ef ? (double)f : std::copysign(0.0, (double)f);
       if (!same_bits(f2d_int(f), want)) bad_f2d++;
     }
-    // double -> float toward zero, flushed below 2^-126, +-inf from 2^128
-    const double x = std::ldexp((double)((int64_t)g()) / 9.3e18, (int)(g() % 300) - 150);
+    // double -> float rounded to nearest even (the host's IEEE conversion),
+    // flushed below 2^-126, +-inf from 2^128; every third input sits exactly
+    // half-way between two floats (the ties-to-even case)
+    double x = std::ldexp((double)((int64_t)g()) / 9.3e18, (int)(g() % 300) - 150);
+    if (it % 3 == 0) {
+      const long long b = __double_as_longlong(x);
+      x = __longlong_as_double((b & ~0x1fffffffLL) | 0x10000000LL);
+    }
     float want = (float)x;
-    if (std::fabs((double)want) > std::fabs(x)) want = std::nextafterf(want, 0.0f);
     if (std::fabs(x) < std::ldexp(1.0, -126)) want = std::copysign(0.0f, (float)x);
     if (std::fabs(x) >= std::ldexp(1.0, 128)) want = std::copysign(INFINITY, (float)x);
     if (!same_bits(d2f_int(x), want)) bad_d2f++;
@@ -320,7 +325,7 @@ int main() {
 
 def test_integer_pipe_conversions(tmp_path):
     """f2d_int is exact for every normal float (subnormals become signed
-    zero); d2f_int rounds toward zero, flushes below 2^-126 and saturates to
+    zero); d2f_int rounds to nearest even, flushes below 2^-126 and saturates to
     +-inf from 2^128, bit for bit against the host's IEEE conversions."""
     gxx = shutil.which("g++")
     if gxx is None:

@@ -1,17 +1,20 @@
-"""The allocation-free entry point mc_p2l_level_noalloc against mc_setup.
+"""The allocation-free entry point mc_p2l_level_noalloc.
 
 Some callers cannot let a library allocate device memory (they hand out
 every byte from their own pool, or allocation would stall the device at the
 wrong time).  They call mc_p2l_level_noalloc with buffers they own; it keeps
 its intermediate sums in a fixed device array of the library.  Its level
-expansions must equal the ones mc_setup stores, within the array tolerance of
-the other parity tests, on two calls in a row (the second call reuses the
-scratch the first one left behind).  This file sorts last so that a run that
-stops at the first failure has already run every other test.
+expansions must equal the oracle's Alg. L.3 expansions and the ones mc_setup
+stores, within the array tolerance of the other parity tests, on two calls in
+a row (the second call reuses the scratch the first one left behind), and
+the calls after the first must leave the device's free memory unchanged.
+This file sorts last so that a run that stops at the first failure has
+already run every other test.
 """
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_2006_16622_gb300 import mcfmm
 from paper_2006_16622_gb300.workloads import uniform_system
 
@@ -42,10 +45,12 @@ def _by_finest_cell(pos, q, box, levels):
 
 
 @pytest.mark.parametrize("bc", [mcfmm.BC_PBC, mcfmm.BC_FREE])
-def test_noalloc_level_expansions_match_setup(bc):
+def test_noalloc_level_expansions_match_oracle(bc):
     import torch
     n, a, L, p = 3000, 14.0, 4, 8
     pos, q = uniform_system(n, a, seed=21)
+    orc = O.System(pos, q, a, L, p, bc=bc)
+    orc.setup()
     ctx = mcfmm.Context(pos, q, a, L, p, bc=bc)
     ctx.setup()
     part, start = _by_finest_cell(pos, q, a, L)
@@ -53,19 +58,33 @@ def test_noalloc_level_expansions_match_setup(bc):
     d_start = torch.tensor(start, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
     lmin = 2 if bc == mcfmm.BC_PBC else 3
-    for _call in range(2):
-        for level in range(lmin, L + 1):
-            nl = 1 << (level - 1)
-            out = torch.full((nl ** 3, (p + 1) ** 2), float("nan"), dtype=torch.float64,
-                             device="cuda")
+    levels = list(range(lmin, L + 1))
+    # every output buffer exists before the first call, so nothing but the
+    # entry point itself runs between the free-memory readings
+    outs = {lv: torch.empty(((1 << (lv - 1)) ** 3, (p + 1) ** 2), dtype=torch.float64,
+                            device="cuda") for lv in levels}
+    free_after_first = None
+    for call in range(2):
+        for level in levels:
+            outs[level].fill_(float("nan"))
+            torch.cuda.synchronize()
+            if free_after_first is not None:
+                assert torch.cuda.mem_get_info()[0] == free_after_first, (call, level)
             rc = mcfmm.p2l_level_noalloc(d_part.data_ptr(), d_start.data_ptr(), n, a, L, level,
-                                         p, bc, out.data_ptr(), stream)
+                                         p, bc, outs[level].data_ptr(), stream)
             assert rc == mcfmm.MC_OK, rc
             torch.cuda.synchronize()
-            ref = ctx.local(level)
-            got = out.cpu().numpy()
+            if free_after_first is None:
+                # the first call may load the module's code; later ones add nothing
+                free_after_first = torch.cuda.mem_get_info()[0]
+            else:
+                assert torch.cuda.mem_get_info()[0] == free_after_first, (call, level)
+            got = outs[level].cpu().numpy()
             assert np.all(np.isfinite(got))
-            assert np.max(np.abs(got - ref)) <= ARR_TOL * np.max(np.abs(ref)), level
+            want = orc.local(level)
+            scale = np.max(np.abs(want))
+            assert np.max(np.abs(got - want)) <= ARR_TOL * scale, (call, level)
+            assert np.max(np.abs(got - ctx.local(level))) <= ARR_TOL * scale, (call, level)
     ctx.close()
 
 
