@@ -733,9 +733,15 @@ __global__ void __launch_bounds__(MC_THREADS)
                 const double* __restrict__ otab, double* __restrict__ Llev) {
   __shared__ McSys S;
   __shared__ unsigned short il[8][189];
+  __shared__ double s_wn[MC_PMAX + 1];  // (-1)^n w^-n, the source scaling
   extern __shared__ double dyn[];
   if (threadIdx.x == 0) S = *sysp;
   il_table_init(il);
+  __syncthreads();
+  if (threadIdx.x <= MC_PMAX) {
+    const int n = threadIdx.x;
+    s_wn[n] = ((n & 1) ? -1.0 : 1.0) * pow(S.lev_w[l], -(double)n);
+  }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int p = S.p, C = S.C;
@@ -799,7 +805,7 @@ __global__ void __launch_bounds__(MC_THREADS)
           int n = (int)sqrtf((float)i + 0.5f);
           while (n * n > i) n--;
           while ((n + 1) * (n + 1) <= i) n++;
-          sg[i] = ok ? ms[i] * ((n & 1) ? -1.0 : 1.0) * pow(w, -(double)n) : 0.0;
+          sg[i] = ok ? ms[i] * s_wn[n] : 0.0;
         }
       }
       __syncthreads();
