@@ -146,6 +146,17 @@ int mc_get_far(mc_ctx *ctx, double *K_out, double *H_out);
  * pair of Alg. 1), else MC_ERR_ARG.  Call mc_setup again afterwards
  * (MC_ERR_STATE until then). */
 int mc_set_lj(mc_ctx *ctx, double eps, double sigma, double cutoff);
+/* Work split of the near-field sum (Alg. 1) in the chain kernels: each of
+ * the 27 near cells is summed by `parts` items per side (2 parts items when
+ * r and r' share their finest cell), each taking every parts-th block of 32
+ * of the cell's charges.  parts = 0 restores the automatic choice made by
+ * mc_init (one item per 48 charges of mean finest-cell occupancy, at most
+ * 4); 1..4 forces it.  The result is the same sum in another order (dE
+ * changes at rounding level only).  MC_ERR_ARG when parts is out of range or
+ * the step's item slots (384) cannot hold 54 parts near items beside the
+ * far-field and expansion items of this (p, L).  used_out (optional, host)
+ * receives the split in force. */
+int mc_set_near_parts(mc_ctx *ctx, int parts, int *used_out);
 /* Multipoles M_n^m of Eq. (4) of every cell of `level` (multipole method
  * only, else MC_ERR_STATE), layout as mc_get_local. */
 int mc_get_multipole(mc_ctx *ctx, int level, double *out);

@@ -198,8 +198,10 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
   const int nF = pbc ? nRB * nfc : 0;
   const int csz = (C + nfc - 1) / nfc;
   const int nE = 4 * nlev;  // E items: four quarter contractions per level
-  // light phase-A slots: F, N (54), X, U; heavy slots: K, E, contributions
-  const int iN = nF, iX = nF + 54, iU = nF + 55, nLA = nF + 56;
+  // light phase-A slots: F, N (54 x near_parts), X, U; heavy slots: K, E,
+  // contributions
+  const int nNP = S.near_parts, nNI = 54 * nNP;
+  const int iN = nF, iX = nF + nNI, iU = iX + 1, nLA = iX + 2;
   const int slotE = nLA;  // partial slots of the E items
   const int nSlots = nLA + nE;
   const int hK = 0, hE = 1, hD = 1 + nE;
@@ -856,13 +858,17 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
               __syncwarp();
             }
           } else if (it < iX) {
-            // ---- N: Alg. 1 over one near cell (27 cells of the extended domain)
+            // ---- N: Alg. 1 over one near cell (27 cells of the extended
+            //      domain), part of its slots: near_parts items per cell and
+            //      side, or 2 near_parts per cell when both sides share it
             ptype = 1;
             const int k0 = it - iN;
-            if (!idle && (!same || k0 < 27)) {
-              const int k = same ? k0 : (k0 % 27);
-              const int side = same ? 2 : (k0 / 27);  // 0 old, 1 new, 2 both
-              if (!item_near<TE>(S, g, off, k, side, pbc, lane,
+            if (!idle) {
+              const int kb = same ? k0 : (k0 % 54);
+              const int k = kb % 27;
+              const int side = same ? 2 : (kb / 27);  // 0 old, 1 new, 2 both
+              const int part = same ? k0 / 27 : k0 / 54, nparts = same ? 2 * nNP : nNP;
+              if (!item_near<TE>(S, g, off, k, side, part, nparts, pbc, lane,
                                  [&](int, int, int) {
                                    const bool okw = need_state();
                                    if (okw && prof_on && lane == 0) prof_item(rp.prof, 14, s_tpub[gi]);

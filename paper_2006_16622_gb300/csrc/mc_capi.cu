@@ -313,6 +313,28 @@ int lattice_table(int dev, int lmax, cudaStream_t stream, const double** out) {
   return MC_OK;
 }
 
+// partial slots per step of the chain kernels with near_parts = P: the
+// barrier-free chain's far items (row blocks x MC_NF_COLS column chunks),
+// 54 P near items, image and log u, four expansion items per level (the
+// phased chain takes fewer); the last slot holds log u itself
+bool near_parts_fit(const McSys& h, int P) {
+  const int nF = h.bc == MC_BC_PBC ? ((h.C + 31) / 32) * MC_NF_COLS : 0;
+  return nF + 54 * P + 2 + 4 * (h.L - h.lmin + 1) <= MC_MAX_ITEMS - 1;
+}
+
+// Near items per cell and side by mean finest-cell occupancy: one item per
+// 48 charges, at most MC_NEAR_PARTS_MAX, within the slot budget.  Alg. 1 is
+// the longest FP64 item of dense cells (about 190 charges at the NaCl
+// full-MC setting, L = 4), so its loop is split there (measured on GB300,
+// FP64 barrier-free chain: 66k / 81k / 84k / 86k MH steps/s for 1..4 items;
+// uniform N = 1e5 at 24 per cell is fastest with one).
+int near_parts_auto(const McSys& h) {
+  const double mean = (double)h.n / (double)std::max(1, h.ncellL);
+  int P = std::min(MC_NEAR_PARTS_MAX, std::max(1, (int)ceil(mean / 48.0)));
+  while (P > 1 && !near_parts_fit(h, P)) P--;
+  return P;
+}
+
 int in_box(const double* x, double a) {
   for (int k = 0; k < 3; k++)
     if (!(x[k] >= 0.0 && x[k] < a)) return 0;
@@ -519,6 +541,7 @@ int mc_init(mc_ctx** out, int64_t n, const double* pos, const double* q, double 
   // is 8-30 % faster in FP64 over N = 1e3..1e6; in FP32-eval the phased one
   // is as fast or faster)
   c->schedule = precision == MC_FP64 ? MC_SCHEDULE_ASYNC : MC_SCHEDULE_PHASED;
+  h.near_parts = near_parts_auto(h);
   DA(c->d_sys, sizeof(McSys));
   DCK(cudaMemcpyAsync(c->d_sys, &h, sizeof(McSys), cudaMemcpyHostToDevice, c->stream));
   DCK(cudaStreamSynchronize(c->stream));
@@ -762,6 +785,18 @@ int mc_set_lj(mc_ctx* c, double eps, double sigma, double cutoff) {
   CK(cudaMemcpyAsync(c->d_sys, &c->h, sizeof(McSys), cudaMemcpyHostToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   c->setup_done = 0;  // the energy changes: set up again
+  return MC_OK;
+}
+
+int mc_set_near_parts(mc_ctx* c, int parts, int* used_out) {
+  if (!c || parts < 0 || parts > MC_NEAR_PARTS_MAX) return MC_ERR_ARG;
+  const int P = parts == 0 ? near_parts_auto(c->h) : parts;
+  if (!near_parts_fit(c->h, P)) return MC_ERR_ARG;
+  CK(cudaSetDevice(c->dev));
+  c->h.near_parts = P;
+  CK(cudaMemcpyAsync(c->d_sys, &c->h, sizeof(McSys), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (used_out) *used_out = P;
   return MC_OK;
 }
 

@@ -315,7 +315,12 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
     };
 
     // ------------------------------------- phase A: propose (+ accept deltas)
-    const int nN = same ? 27 : 54;
+    // near items: near_parts per cell and side (slot blocks of the cell
+    // round robin), 2 near_parts per cell when r and r' share their finest
+    // cell (27 items at near_parts = 1)
+    const int nNP = S.near_parts;
+    const int nNsame = nNP == 1 ? 1 : 2 * nNP;
+    const int nN = same ? 27 * nNsame : 54 * nNP;
     // the multipole method's P items: 95 per level (entries 2k, 2k+1 of
     // IL(alpha) and IL(alpha') per item, one per 8-lane group)
     const int nEx = mm ? 95 * nlev : nE;
@@ -647,9 +652,11 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
         // ---- N: Alg. 1 over one near cell (27 cells of the extended domain)
         ptype = 1;
         const int k0 = it - iN;
-        const int k = same ? k0 : (k0 % 27);
-        const int side = same ? 2 : (k0 / 27);  // 0 old, 1 new, 2 both
-        item_near<TE>(S, g, s_off, k, side, pbc, lane,
+        const int kb = same ? k0 : (k0 % 54);
+        const int k = kb % 27;
+        const int side = same ? 2 : (kb / 27);  // 0 old, 1 new, 2 both
+        const int part = same ? k0 / 27 : k0 / 54, nparts = same ? nNsame : nNP;
+        item_near<TE>(S, g, s_off, k, side, part, nparts, pbc, lane,
                       [&](int, int, int) {
                         need_state();
                         return true;

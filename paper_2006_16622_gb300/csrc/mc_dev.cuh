@@ -29,7 +29,8 @@
 #define MC_MAXLEV 8
 #define MC_THREADS 256
 #define MC_WARPS (MC_THREADS / 32)
-#define MC_MAX_ITEMS 256
+#define MC_MAX_ITEMS 384  // partial slots per step (the last one holds log u)
+#define MC_NEAR_PARTS_MAX 4  // items per near cell and side (McSys.near_parts)
 #define MC_NF_ROWS 6    // far-field row blocks of 32 rows (covers C <= 192)
 #define MC_NF_COLS 16   // far-field column chunks (maximum; RunParams.nf_cols <= this)
 #define MC_GPRE 16      // far-operator columns a warp keeps in registers
@@ -88,6 +89,10 @@ struct McSys {
   // for r^2 < rc2, between different particles of the near cells
   int lj_on;
   double lj_eps4, lj_s6, lj_s12, lj_rc2;
+  // Alg. 1 split: each near cell's slots are shared by near_parts items per
+  // side (2 near_parts items when r and r' share their finest cell), slot
+  // blocks of 32 taken round robin; 1..MC_NEAR_PARTS_MAX
+  int near_parts;
 };
 
 struct RunParams {

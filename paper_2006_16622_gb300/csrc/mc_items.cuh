@@ -52,12 +52,15 @@ constexpr double kInf = __builtin_huge_val();
 // Alg. 1 over one near cell: the neighbour at offset k (0..26) of the
 // finest cell of r (side 0), of r' (side 1), or of both (side 2, same
 // cell): the Coulomb (and Lennard-Jones) change of the moving charge with
-// the cell's charges; +inf when r' falls on a charge.  wait(c0, c1, c2) is
-// called with the (wrapped) cell before its list is read.
+// the cell's charges; +inf when r' falls on a charge.  The item takes the
+// slot blocks part, part + nparts, ... (32 slots each) of the cell, so
+// nparts items together cover it.  wait(c0, c1, c2) is called with the
+// (wrapped) cell before its list is read.
 template <typename TE, typename Wait>
 __device__ __forceinline__ bool item_near(const McSys& S, const StepGeo& g,
                                           const double (*off)[MC_MAXLEV + 2][3], int k, int side,
-                                          bool pbc, int lane, Wait&& wait, double* partial_out) {
+                                          int part, int nparts, bool pbc, int lane, Wait&& wait,
+                                          double* partial_out) {
   const int L = S.L;
   const int* cc = (side == 1) ? g.cfn : g.cf;
   const int d0 = k / 9 - 1, d1 = (k / 3) % 3 - 1, d2 = k % 3 - 1;
@@ -92,7 +95,7 @@ __device__ __forceinline__ bool item_near(const McSys& S, const StepGeo& g,
       const double ox = g.r[0] - sx, oy = g.r[1] - sy, oz = g.r[2] - sz;
       const double nx = g.rn[0] - sx, ny = g.rn[1] - sy, nz = g.rn[2] - sz;
       double acc = 0.0;
-      for (int s = lane; s < cnt; s += 32) {
+      for (int s = 32 * part + lane; s < cnt; s += 32 * nparts) {
         const double4 xi = ldcg4(&S.cpos[(size_t)cell * S.cap + s]);
         const int pid = (side != 1 || lj) ? __ldcg(&S.cpid[(size_t)cell * S.cap + s]) : -1;
         if (side != 1) {
@@ -140,7 +143,7 @@ __device__ __forceinline__ bool item_near(const McSys& S, const StepGeo& g,
       const float close2 = d2f_int(wL * wL * (1.0 / 64.0));
       double acc64 = 0.0;
       bool any_close = false;
-      for (int s = lane; s < cnt; s += 32) {
+      for (int s = 32 * part + lane; s < cnt; s += 32 * nparts) {
         const float4 xi = __ldcg(&S.cpos32[(size_t)cell * S.cap + s]);
         const int pid = (side != 1 || lj) ? __ldcg(&S.cpid[(size_t)cell * S.cap + s]) : -1;
         bool close_o = false, close_n = false;

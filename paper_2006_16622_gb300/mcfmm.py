@@ -28,7 +28,8 @@ EXPORTED = ["mc_init", "mc_setup", "mc_propose", "mc_accept", "mc_run", "mc_ener
             "mc_destroy", "mc_strerror", "mc_p2l_level_noalloc", "mc_batch_create",
             "mc_batch_tune", "mc_batch_run", "mc_batch_info", "mc_batch_destroy",
             "mc_set_schedule", "mc_set_ctas", "mc_batch_set_schedule", "mc_inject_wait_fault",
-            "mc_get_multipole", "mc_set_lj", "mc_step_counter", "mc_probe_fma_rate"]
+            "mc_get_multipole", "mc_set_lj", "mc_step_counter", "mc_probe_fma_rate",
+            "mc_set_near_parts"]
 
 
 class McStats(ctypes.Structure):
@@ -69,6 +70,7 @@ def load(path: str = LIB_PATH):
     L.mc_get_local.argtypes = [P, I, P]
     L.mc_get_multipole.argtypes = [P, I, P]
     L.mc_set_lj.argtypes = [P, D, D, D]
+    L.mc_set_near_parts.argtypes = [P, I, P]
     L.mc_get_far.argtypes = [P, P, P]
     L.mc_lattice_sums.argtypes = [I, P]
     L.mc_status.argtypes = [P]
@@ -220,6 +222,13 @@ class Context:
 
     def set_lj(self, eps, sigma, cutoff):
         _check(load().mc_set_lj(self._h, float(eps), float(sigma), float(cutoff)), "mc_set_lj")
+
+    def set_near_parts(self, parts=0):
+        """Near-field (Alg. 1) items per cell and side; 0 = automatic.
+        Returns the split in force."""
+        out = np.zeros(1, dtype=np.int32)
+        _check(load().mc_set_near_parts(self._h, int(parts), _ptr(out)), "mc_set_near_parts")
+        return int(out[0])
 
     def multipole(self, level):
         nl = 1 << (level - 1)
