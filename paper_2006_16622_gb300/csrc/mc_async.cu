@@ -102,8 +102,11 @@ __device__ __forceinline__ bool flag_wait(volatile long long* f, long long v, vo
 }
 
 // one warp waits for a global counter to reach target (lane 0 polls with
-// relaxed loads and back-off, bounded by wait_ns; acquire fence once
-// reached); false on timeout or when another CTA has set an error status
+// relaxed loads and back-off, bounded by wait_ns; an acquire-only fence once
+// reached: it orders the warp's later accesses after the writes released
+// with the counted arrivals, without waiting for the warp's own earlier
+// writes as an acq_rel fence would); false on timeout or when another CTA
+// has set an error status
 __device__ __forceinline__ bool counter_wait(unsigned long long* ctr, unsigned long long target,
                                              int* status, long long wait_ns) {
   int ok = 1;
@@ -129,7 +132,7 @@ __device__ __forceinline__ bool counter_wait(unsigned long long* ctr, unsigned l
         }
       }
     }
-    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    asm volatile("fence.acquire.gpu;" ::: "memory");
   }
   ok = __shfl_sync(0xffffffffu, ok, 0);
   __syncwarp();
@@ -402,6 +405,7 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
       const unsigned long long dprev = t > 0 ? cumD[(t - 1) & 3] : 0ull;
       double v[MC_MAX_ITEMS / 32];
       double lu = 0.0;
+      const int nRows = (nSlots + 31) / 32;  // warp-uniform
       {
         const unsigned long long t0 = mc_globaltimer();
         unsigned spins = 0;
@@ -441,21 +445,18 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
           }
         }
         if (!ok) break;
-        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        asm volatile("fence.acquire.gpu;" ::: "memory");
       }
-      double acc = 0.0;
+      // the same fixed order in every CTA; only the rows that hold slots
+      // (every FP64 add here is on the step's critical path)
+      double acc = v[0];
 #pragma unroll
-      for (int i = 0; i < MC_MAX_ITEMS / 32; i++) acc += v[i];
+      for (int i = 1; i < MC_MAX_ITEMS / 32; i++)
+        if (i < nRows) acc += v[i];
       const double dE = warp_sum(acc);
       lu = __shfl_sync(0xffffffffu, lu, 0);
-      bool accept;
-      if (dE <= 0.0) {
-        accept = true;
-      } else {
-        const double t2 = -rp.beta * dE;
-        accept = lu < t2;
-        if (fabs(lu - t2) < 1e-9 * fmax(1.0, fabs(t2))) n_border++;
-      }
+      const double t2 = -rp.beta * dE;
+      const bool accept = dE <= 0.0 || lu < t2;
       if (accept && !nomove) cumB += (unsigned long long)nB;
       if (lane == 0) {
         s_dEu[t & 7] = dE;
@@ -478,6 +479,8 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
         }
       }
       __syncwarp();
+      // decisions within 1e-9 of the threshold (counted after publishing)
+      if (dE > 0.0 && fabs(lu - t2) < 1e-9 * fmax(1.0, fabs(t2))) n_border++;
       if (!idle) cumD[t & 3] += (unsigned long long)nDs;
       steps_done++;
       if (accept) n_acc++;
@@ -970,6 +973,18 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
                 }
               }
             }
+            if (a >= 0) {
+              // the accepted values, formed before the decision is known: an
+              // accept then only stores them
+#pragma unroll
+              for (int h2 = 0; h2 < 2; h2++) {
+#pragma unroll
+                for (int i = 0; i < 8; i++) {
+                  const int kk = lane + 32 * i;
+                  if (own[h2] && kk < C) v[h2][i] = fma(s_P[kk], w[h2][i] + w1[h2][i], v[h2][i]);
+                }
+              }
+            }
             if (!decided) {
               if (!flag_wait(&s_dstep, t, &s_abort, S.status, rp.wait_ns)) {
                 fail = true;
@@ -992,14 +1007,14 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
               // ---- K += dK, H += G dK (sum of the column-block partials)
               item_kh(S, b - 1, nfc, S.gK + (size_t)(t & 3) * MC_NF_COLS * C, S.dK + (size_t)(t & 3) * C, lane);
             } else {
-              // L += P (sum of the contributions), the loaded operands
+              // L += P (sum of the contributions), formed above
               ptype = lsm ? 5 : 4;
 #pragma unroll
               for (int h2 = 0; h2 < 2; h2++) {
 #pragma unroll
                 for (int i = 0; i < 8; i++) {
                   const int kk = lane + 32 * i;
-                  if (own[h2] && kk < C) __stcg(&Lt[h2][kk], fma(s_P[kk], w[h2][i] + w1[h2][i], v[h2][i]));
+                  if (own[h2] && kk < C) __stcg(&Lt[h2][kk], v[h2][i]);
                 }
               }
             }

@@ -725,9 +725,12 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
         v[i] = ii < (mm ? nCTA : nProp) ? __ldcg(&part[ii]) : 0.0;
       }
       const double lu = (rp.mode == 0 && lane == 0) ? __ldcg(&part[MC_MAX_ITEMS - 1]) : 0.0;
-      double acc = 0.0;
+      // only the rows that hold slots (warp-uniform count)
+      const int nRows = ((mm ? nCTA : nProp) + 31) / 32;
+      double acc = v[0];
 #pragma unroll
-      for (int i = 0; i < MC_MAX_ITEMS / 32; i++) acc += v[i];
+      for (int i = 1; i < MC_MAX_ITEMS / 32; i++)
+        if (i < nRows) acc += v[i];
       acc = warp_sum(acc);
       if (lane == 0) {
         s_dE = acc;

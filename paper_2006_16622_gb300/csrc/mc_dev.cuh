@@ -154,6 +154,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* ctr, unsigned l
     unsigned spins = 0;
     // poll with relaxed loads (an acquire per poll would invalidate the SM's
     // L1 for every warp on it); one acquire fence once the count is reached
+    // (acquire only: this thread's own writes were released by its arrival)
     while (true) {
       asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
       if (v >= target) break;
@@ -169,7 +170,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* ctr, unsigned l
         }
       }
     }
-    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    asm volatile("fence.acquire.gpu;" ::: "memory");
     s_ok = ok;
   }
   __syncthreads();
@@ -210,7 +211,7 @@ __device__ __forceinline__ bool warp_wait(unsigned long long* ctr, unsigned long
         }
       }
     }
-    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    asm volatile("fence.acquire.gpu;" ::: "memory");
   }
   ok = __shfl_sync(0xffffffffu, ok, 0);
   __syncwarp();
