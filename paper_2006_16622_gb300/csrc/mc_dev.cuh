@@ -34,10 +34,11 @@
 #define MC_NF_ROWS 6    // far-field row blocks of 32 rows (covers C <= 192)
 #define MC_NF_COLS 16   // far-field column chunks (maximum; RunParams.nf_cols <= this)
 #define MC_GPRE 16      // far-operator columns a warp keeps in registers
-// CTAs per SM of the batched form's kernels, by evaluation type (registers
-// per thread capped at 256 / this; measured on GB300 with 64 chains: FP64
-// best at 2, FP32-eval at 3; the single-chain kernels keep one CTA per SM)
-#define MC_BATCH_CTAS_PER_SM(TE) (sizeof(TE) == 8 ? 2 : 3)
+// CTAs per SM of the batched form's kernels (registers per thread capped at
+// 256 / this; measured on GB300 with 64 chains: 3 for both evaluation types,
+// FP64 with the pair-of-floats contributions 557k -> 572k MH steps/s from 2
+// to 3, 527k at 4; the single-chain kernels keep one CTA per SM)
+#define MC_BATCH_CTAS_PER_SM(TE) 3
 #define MC_VAR_PLAIN 0  // chain kernel variants (see chain_body)
 #define MC_VAR_SPEC 1
 #define MC_VAR_MM 2
