@@ -99,9 +99,14 @@ double scale_of(int k) {
 }
 
 // chunks of the interaction list per target on level l (1 = write in place)
+// chunks per target cell of the Alg. L.3 gather on level l: about eight
+// equal tasks per resident warp (one CTA per SM), at most one chunk per
+// source unit (189 finest cells of the list per target and level cell)
 int chunks_for_level(const McSys& h, int sms, int l, size_t max_doubles) {
   const long long ncl = (long long)h.lev_n[l] * h.lev_n[l] * h.lev_n[l];
-  long long nchunk = std::min<long long>(189, std::max<long long>(1, (4LL * sms * MC_WARPS + ncl - 1) / ncl));
+  const long long f = 1LL << (h.L - l);
+  const long long units = 189LL * f * f * f;
+  long long nchunk = std::min<long long>(units, std::max<long long>(1, (8LL * sms * MC_WARPS + ncl - 1) / ncl));
   if (nchunk > 1 && (size_t)(ncl * nchunk * h.C) > max_doubles)
     nchunk = std::max<long long>(1, (long long)(max_doubles / ((size_t)ncl * h.C)));
   return (int)nchunk;

@@ -67,21 +67,26 @@ __global__ void k_max_int(int n, const int* __restrict__ v, int* __restrict__ ou
 }
 
 // -------------------------------------------- Alg. L.3 as a per-target gather
-// Each warp task is (target cell t of level l, chunk of t's interaction
-// list).  By the symmetry of the interaction list, the cells whose lists
-// contain t are exactly t's own list (with the opposite image shift), so
+// Each warp task is (target cell t of level l, chunk of t's source units).
+// By the symmetry of the interaction list, the cells whose lists contain t
+// are exactly t's own list (with the opposite image shift), so
 //   Lhat_t = sum_{e in IL(t)} sum_{i in cell(e)} q_i conj It(r_i + shift a - R_t).
-// Two particles per warp step (one per half-warp, lane = column m).
-// Partial expansions of the chunks go to `out` ([t][chunk][C]), reduced in a
-// fixed order by k_reduce_chunks.
+// A source unit is one finest cell of one list entry (189 f^3 units per
+// target, f = 2^(L-l) finest cells per axis of a level-l cell), so chunks
+// have equal work on every level.  Four charges per warp step (one per
+// group of 8 lanes).  Partial expansions of the chunks go to `out`
+// ([t][chunk][C]), reduced in a fixed order by k_reduce_chunks.
 __global__ void __launch_bounds__(MC_THREADS)
     k_p2l_level(const McSys* __restrict__ sysp, int l, int nchunk, double* __restrict__ out) {
   __shared__ McSys S;
   __shared__ HarmTabs<double> tabs;
   __shared__ unsigned short il[8][189];
   __shared__ double stage[MC_WARPS][256];
+  __shared__ double s_iW[MC_PMAX + 1][16];
+  __shared__ double s_P[(MC_PMAX + 1) * (MC_PMAX + 1)];
   if (threadIdx.x == 0) S = *sysp;
   harm_tabs_init<double>(&tabs);
+  irregular_w_tabs<double>(s_iW, s_P);
   il_table_init(il);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane >> 3;
@@ -90,7 +95,9 @@ __global__ void __launch_bounds__(MC_THREADS)
   const int nl = S.lev_n[l], f = 1 << (L - l), nL = S.nL;
   const double w = S.lev_w[l];
   const int ntask = nl * nl * nl * nchunk;
-  const int per = (189 + nchunk - 1) / nchunk;
+  const int f3 = f * f * f;
+  const long long units = 189LL * f3;
+  const long long per = (units + nchunk - 1) / nchunk;
   for (int task = blockIdx.x * MC_WARPS + warp; task < ntask; task += gridDim.x * MC_WARPS) {
     const int t = task / nchunk, ch = task % nchunk;
     const int tc[3] = {t / (nl * nl), (t / nl) % nl, t % nl};
@@ -99,8 +106,13 @@ __global__ void __launch_bounds__(MC_THREADS)
     double ar[MC_PMAX + 2], ai[MC_PMAX + 2];
 #pragma unroll
     for (int q = 0; q <= MC_PMAX + 1; q++) ar[q] = ai[q] = 0.0;
-    const int kb = ch * per, ke = min(189, kb + per);
+    const long long ub = (long long)ch * per, ue = min(units, ub + per);
+    // units [ub, ue): list entries kb..ke-1; of each entry the finest cells
+    // fcb..fce-1 (all but possibly the first and last entry: every one)
+    const int kb = (int)(ub / f3), ke = ue > ub ? (int)((ue - 1) / f3) + 1 : kb;
     for (int k = kb; k < ke; k++) {
+      const int fcb = (int)max(0LL, ub - (long long)k * f3);
+      const int fce = (int)min((long long)f3, ue - (long long)k * f3);
       int ox, oy, oz;
       il_unpack(il[par][k], &ox, &oy, &oz);
       const int e[3] = {tc[0] + ox, tc[1] + oy, tc[2] + oz};
@@ -118,8 +130,8 @@ __global__ void __launch_bounds__(MC_THREADS)
       }
       if (!ok) continue;
       const double bx = shift[0] - Rt[0], by = shift[1] - Rt[1], bz = shift[2] - Rt[2];
-      // the finest cells inside the source cell; four charges per step
-      for (int fc = 0; fc < f * f * f; fc++) {
+      // this chunk's finest cells of the source cell; four charges per step
+      for (int fc = fcb; fc < fce; fc++) {
         const int gx = src[0] * f + fc / (f * f), gy = src[1] * f + (fc / f) % f,
                   gz = src[2] * f + fc % f;
         const int cell = (gx * nL + gy) * nL + gz;
@@ -133,11 +145,13 @@ __global__ void __launch_bounds__(MC_THREADS)
           const double dy = act ? v.y + by : 3.0;
           const double dz = act ? v.z + bz : 3.0;
           const double qi = act ? v.w : 0.0;
-          irregular_group<double>(&tabs, p, dx, dy, dz,
-                                  [&](int t2, int n, int m, bool vld, double cr, double ci) {
-                                    ar[t2] += qi * cr;
-                                    ai[t2] -= qi * ci;
-                                  });
+          // column-scaled irregular set with the charge folded into its start
+          // value (value (n, m) / P_n^m); P_n^m is applied once per chunk
+          irregular_group_w<double>(&tabs, s_iW, p, dx, dy, dz, qi,
+                                    [&](int t2, int n, int m, bool vld, double cr, double ci) {
+                                      ar[t2] += cr;
+                                      ai[t2] -= ci;
+                                    });
         }
       }
     }
@@ -154,8 +168,8 @@ __global__ void __launch_bounds__(MC_THREADS)
       group_nm(p, t2, &n, &m, &vld);
       if (grp == 0 && vld) {
         const int kk = rl_re(n, m);
-        st[kk] = vr;
-        if (m) st[kk + 1] = vi;
+        st[kk] = vr * s_P[kk];
+        if (m) st[kk + 1] = vi * s_P[kk + 1];
       }
     }
     __syncwarp();
