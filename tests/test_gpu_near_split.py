@@ -9,8 +9,9 @@ both chain schedules: every dE within 1e-10 max(1, |dE|) of the oracle's
 chain and every decision identical.  The same with the Lennard-Jones term on
 a perturbed NaCl crystal (64 ions per finest cell), in FP32-eval (the
 oracle follows the GPU's decisions; beta |d dE| with p95 <= 1e-4 and max <=
-1e-3), and in the batched form with a forced split per chain.  The split
-changes the order of the near sum only.
+1e-3), in the batched form with a forced split per chain, and in the
+multipole method's chain.  The split changes the order of the near sum
+only.
 """
 import numpy as np
 import pytest
@@ -156,3 +157,21 @@ def test_batch_with_forced_split_replays_oracle():
     b.close()
     for c in ctxs:
         c.close()
+
+
+def test_multipole_method_split_replays_oracle(dense):
+    """The multipole method's chain (Alg. M.1-M.3) shares the near-field
+    items: forced splits replay the oracle's multipole chain."""
+    pos, q, _, _, _ = dense
+    o = O.System(pos, q, A, L, P_EXP)
+    o.setup_multipole()
+    steps = 600
+    ro = o.run(steps, seed=8, step0=0, beta=1.0, half_width=H)
+    for parts in (2, 4):
+        g = mcfmm.Context(pos, q, A, L, P_EXP)
+        g.set_near_parts(parts)
+        g.setup(mcfmm.SETUP_MULTIPOLE)
+        rg = g.run(steps, seed=8, beta=1.0, half_width=H, log=True)
+        _check_replay(rg, ro)
+        assert np.array_equal(g.positions(), o.positions())
+        g.close()
