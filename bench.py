@@ -825,22 +825,30 @@ def gpu_arm(args):
 
     # end to end through the C ABI: host arrays in, positions and energy out
     e2e = None
+    e2e_fast = None
     if not args.no_e2e:
         torch.cuda.synchronize()
-        t_e2e = []
-        for i in range(2):
-            t0 = time.perf_counter()
-            ctx = mcfmm.Context(pos, q, W.a, W.levels, W.p, precision=mcfmm.FP64,
-                                stream=stream.cuda_stream)
-            ctx.setup()
-            ctx.run(S, seed=replica_seed(W.seed + 7, rank), beta=W.beta, half_width=W.half_width,
-                    stats=False)
-            out_pos = ctx.positions()
-            e = ctx.energy()
-            ctx.close()
-            t_e2e.append(time.perf_counter() - t0)
-            assert np.isfinite(e) and out_pos.shape == pos.shape
-        te = max_over_ranks(max(t_e2e[1:]) if len(t_e2e) > 1 else t_e2e[0], dist, "cuda")
+
+        def e2e_jobs(mode):
+            t_e2e = []
+            for i in range(2):
+                t0 = time.perf_counter()
+                ctx = mcfmm.Context(pos, q, W.a, W.levels, W.p, precision=mcfmm.FP64,
+                                    stream=stream.cuda_stream)
+                ctx.setup(mode)
+                ctx.run(S, seed=replica_seed(W.seed + 7, rank), beta=W.beta,
+                        half_width=W.half_width, stats=False)
+                out_pos = ctx.positions()
+                e = ctx.energy()
+                ctx.close()
+                t_e2e.append(time.perf_counter() - t0)
+                assert np.isfinite(e) and out_pos.shape == pos.shape
+            return max_over_ranks(max(t_e2e[1:]) if len(t_e2e) > 1 else t_e2e[0], dist, "cuda")
+
+        te = e2e_jobs(mcfmm.SETUP_P2L)
+        # the same jobs with the fast (FMM-variant) setup: expansions equal to
+        # Alg. L.3's up to the multipole truncation (detail line only)
+        e2e_fast = whole_job_rate(S, world, e2e_jobs(mcfmm.SETUP_FMM))
         e2e = {"value": whole_job_rate(S, world, te), "unit": UNIT,
                "h2d_bytes_per_step": int(pos.nbytes + q.nbytes),
                "d2h_bytes_per_step": int(len(q) * 32 + 8),
@@ -879,6 +887,7 @@ def gpu_arm(args):
                            "sample": f"batched oracle leg failed: {ex!r}"}
     forms = {"fp64": value}
     detail = {"mh_steps_per_step": S, "fp64_setup_s": r64["setup_s"],
+              "e2e_fast_setup": e2e_fast,
               "roofline_flops_per_mh_step": F, "fp64_acceptance": r64["nu"],
               "peaks_measured_tflops": {"fp64": fp64_meas / 1e12, "fp32": fp32_meas / 1e12}}
     if r32:

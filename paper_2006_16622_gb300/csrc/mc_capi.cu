@@ -41,8 +41,9 @@ __global__ void k_lattice_sums(int, double*);
 __global__ void k_far_operator(int, double, const double*, double*);
 __global__ void k_p2m_level(const McSys*, int, int, double*);
 __global__ void k_offset_table(int, double*);
-cudaError_t m2l_launch(const McSys*, int, int, int, int, const double*, const double*, double*,
-                       cudaStream_t);
+cudaError_t m2l_launch(const McSys*, int, int, int, int, const double*, const double*, double*, double*,
+                       size_t, cudaStream_t);
+int m2l_offset_chunks(int nl, int sms);
 
 struct mc_ctx {
   McSys h;        // host copy holding device pointers
@@ -269,7 +270,8 @@ int run_setup_fmm(mc_ctx* c) {
   if (rc != MC_OK) return rc;
   for (int l = h.lmin; l <= h.L; l++) {
     CK(m2l_launch(c->d_sys, p, l, h.lev_n[l], c->sms, c->d_mpole + (size_t)h.lev_off[l] * C,
-                  c->d_otab, h.Lhat + (size_t)h.lev_off[l] * C, c->stream));
+                  c->d_otab, h.Lhat + (size_t)h.lev_off[l] * C, c->d_scratch, c->scratch_doubles,
+                  c->stream));
   }
   const int nch = std::min<int>(1024, std::max<int>(1, h.n / 64));
   k_box_multipole<<<grid_for(c->sms, nch, MC_WARPS), MC_THREADS, 0, c->stream>>>(c->d_sys, nch,
@@ -522,6 +524,9 @@ int mc_init(mc_ctx** out, int64_t n, const double* pos, const double* q, double 
     const size_t ncl = (size_t)h.lev_n[l] * h.lev_n[l] * h.lev_n[l];
     const int nchunk = chunks_for_level(h, c->sms, l, kScratchCap);
     if (nchunk > 1) need = std::max(need, ncl * nchunk * C);
+    // offset chunks of the fast setup's multipole-to-local pass
+    const size_t nco = (size_t)m2l_offset_chunks(h.lev_n[l], c->sms);
+    if (nco > 1) need = std::max(need, std::min(ncl * nco * C, kScratchCap));
   }
   need = std::max(need, (size_t)1024 * (C + 3));
   need = std::max(need, (size_t)c->sms * 2 * MC_WARPS);

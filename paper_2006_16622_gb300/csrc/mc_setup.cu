@@ -732,9 +732,12 @@ __global__ void k_offset_table(int p, double* __restrict__ out) {
 // each (j, k; n, m > 0) needs four real coefficients, shared by the
 // MC_M2L_G targets a lane carries.
 // A CTA takes MC_M2L_T targets of one parity class, which share the 189
-// offsets: each offset's It table is staged once per CTA, each warp stages
-// its targets' source multipoles (scaled by (-1/w)^n), and lane q computes
-// the outputs q, q + 32, ... (j, k >= 0) of its warp's targets.
+// offsets, and one chunk of those offsets: each offset's It table is staged
+// once per CTA, each warp stages its targets' source multipoles (scaled by
+// (-1/w)^n), and lane q computes the outputs q, q + 32, ... (j, k >= 0) of
+// its warp's targets.  With nco > 1 offset chunks (the small levels, whose
+// few targets would otherwise leave most SMs idle) each chunk's sums go to
+// part[(cell * nco + chunk) * C], reduced in chunk order by k_reduce_chunks.
 #define MC_M2L_G 4
 #define MC_M2L_T (MC_WARPS * MC_M2L_G)
 __device__ __forceinline__ double flip_sign(double x, unsigned long long mask) {
@@ -744,7 +747,8 @@ __device__ __forceinline__ double flip_sign(double x, unsigned long long mask) {
 template <int NS>
 __global__ void __launch_bounds__(MC_THREADS)
     k_m2l_level(const McSys* __restrict__ sysp, int l, const double* __restrict__ Mlev,
-                const double* __restrict__ otab, double* __restrict__ Llev) {
+                const double* __restrict__ otab, double* __restrict__ Llev, int nco,
+                double* __restrict__ part) {
   __shared__ McSys S;
   __shared__ unsigned short il[8][189];
   __shared__ double s_wn[MC_PMAX + 1];  // (-1)^n w^-n, the source scaling
@@ -777,9 +781,13 @@ __global__ void __launch_bounds__(MC_THREADS)
   }
   const int per_class = h * h * h;
   const int chunks = (per_class + MC_M2L_T - 1) / MC_M2L_T;
-  for (int task = blockIdx.x; task < 8 * chunks; task += gridDim.x) {
-    const int cls = task / chunks;
-    const int i0 = (task % chunks) * MC_M2L_T + warp * MC_M2L_G;
+  const int per_o = (189 + nco - 1) / nco;
+  for (int task = blockIdx.x; task < 8 * chunks * nco; task += gridDim.x) {
+    const int oc = task % nco, tk = task / nco;
+    const int cls = tk / chunks;
+    const int i0 = (tk % chunks) * MC_M2L_T + warp * MC_M2L_G;
+    const bool warp_has = i0 < per_class;  // warp-uniform
+    const int eb = oc * per_o, ee = min(189, eb + per_o);
     const int bx = (cls >> 2) & 1, by = (cls >> 1) & 1, bz = cls & 1;
     int tgt[MC_M2L_G][3];
 #pragma unroll
@@ -794,7 +802,7 @@ __global__ void __launch_bounds__(MC_THREADS)
     for (int u = 0; u < NS; u++)
 #pragma unroll
       for (int g = 0; g < MC_M2L_G; g++) accr[u][g] = acci[u][g] = 0.0;
-    for (int e = 0; e < 189; e++) {
+    for (int e = eb; e < ee; e++) {
       int ox, oy, oz;
       il_unpack(il[cls][e], &ox, &oy, &oz);
       __syncthreads();  // previous offset's tables are consumed
@@ -825,7 +833,7 @@ __global__ void __launch_bounds__(MC_THREADS)
       __syncthreads();
 #pragma unroll
       for (int u = 0; u < NS; u++) {
-        if (lane + 32 * u >= nout) continue;
+        if (!warp_has || lane + 32 * u >= nout) continue;
         const int j = qj[u], k = qk[u];
         for (int n = 0; n <= p; n++) {
           const int L2 = j + n;
@@ -860,7 +868,8 @@ __global__ void __launch_bounds__(MC_THREADS)
 #pragma unroll
     for (int g = 0; g < MC_M2L_G; g++) {
       if (i0 + g >= per_class) continue;
-      double* o = Llev + (size_t)((tgt[g][0] * nl + tgt[g][1]) * nl + tgt[g][2]) * C;
+      const size_t cell = (size_t)((tgt[g][0] * nl + tgt[g][1]) * nl + tgt[g][2]);
+      double* o = nco > 1 ? part + (cell * nco + oc) * C : Llev + cell * C;
 #pragma unroll
       for (int u = 0; u < NS; u++) {
         if (lane + 32 * u >= nout) continue;
@@ -879,12 +888,26 @@ size_t m2l_smem_bytes(int p) {
   return sizeof(double) * (2 * (size_t)per + (size_t)MC_WARPS * MC_M2L_G * C);
 }
 
-// launches the multipole-to-local pass of one level
-cudaError_t m2l_launch(const McSys* d_sys, int p, int l, int nl, int sms, const double* M,
-               const double* otab, double* Lout, cudaStream_t st) {
-  const int nout = (p + 1) * (p + 2) / 2, ns = (nout + 31) / 32;
+// offset chunks of the multipole-to-local pass on a level with nl cells per
+// axis: about two tasks per SM (1 on the large levels)
+int m2l_offset_chunks(int nl, int sms) {
   const int h = nl / 2, chunks = (h * h * h + MC_M2L_T - 1) / MC_M2L_T;
-  const int grid = std::max(1, std::min(8 * chunks, sms * 4));
+  const int want = (2 * sms + 8 * chunks - 1) / (8 * chunks);
+  return std::max(1, std::min(189, want));
+}
+
+// launches the multipole-to-local pass of one level (scratch: room for the
+// offset chunks' partial sums, ncl x nco x C doubles)
+cudaError_t m2l_launch(const McSys* d_sys, int p, int l, int nl, int sms, const double* M,
+               const double* otab, double* Lout, double* scratch, size_t scratch_doubles,
+               cudaStream_t st) {
+  const int nout = (p + 1) * (p + 2) / 2, ns = (nout + 31) / 32;
+  const int C = (p + 1) * (p + 1);
+  const int h = nl / 2, chunks = (h * h * h + MC_M2L_T - 1) / MC_M2L_T;
+  const size_t ncl = (size_t)nl * nl * nl;
+  int nco = m2l_offset_chunks(nl, sms);
+  while (nco > 1 && ncl * nco * C > scratch_doubles) nco--;
+  const int grid = std::max(1, std::min(8 * chunks * nco, sms * 4));
   const size_t smem = m2l_smem_bytes(p);
   cudaError_t e = cudaSuccess;
 #define MC_M2L_CASE(NS_)                                                                   \
@@ -892,7 +915,7 @@ cudaError_t m2l_launch(const McSys* d_sys, int p, int l, int nl, int sms, const 
     e = cudaFuncSetAttribute(k_m2l_level<NS_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                              (int)smem);                                                   \
     if (e == cudaSuccess) {                                                                \
-      k_m2l_level<NS_><<<grid, MC_THREADS, smem, st>>>(d_sys, l, M, otab, Lout);           \
+      k_m2l_level<NS_><<<grid, MC_THREADS, smem, st>>>(d_sys, l, M, otab, Lout, nco, scratch); \
       e = cudaGetLastError();                                                              \
     }                                                                                      \
     break;
@@ -906,5 +929,10 @@ cudaError_t m2l_launch(const McSys* d_sys, int p, int l, int nl, int sms, const 
       e = cudaErrorInvalidValue;
   }
 #undef MC_M2L_CASE
+  if (e == cudaSuccess && nco > 1) {
+    const int rb = (int)std::min<size_t>((ncl * C + 255) / 256, (size_t)sms * 8);
+    k_reduce_chunks<<<std::max(1, rb), 256, 0, st>>>((int)ncl, nco, C, scratch, Lout);
+    e = cudaGetLastError();
+  }
   return e;
 }
