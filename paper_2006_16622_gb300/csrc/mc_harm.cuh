@@ -247,6 +247,18 @@ __device__ __forceinline__ void irregular_group_w(const HarmTabs<T>* t, const T 
                                 static_cast<F&&>(use));
 }
 
+// The same column-scaled sets with the step loop unrolled: for consumers
+// that keep the values in register arrays indexed by the step.
+template <typename T, typename F>
+__device__ __forceinline__ void irregular_group_wu(const HarmTabs<T>* t, const T (*W)[16], int p, T x,
+                                                   T y, T z, T s, F&& use) {
+  const T r2 = x * x + y * y + z * z;
+  const T ir = mc_rsqrt(r2);
+  const T ir2 = ir * ir;
+  harm_group<T, F, true, true>(t->iA, W, p, x * ir2, y * ir2, z * ir2, ir2, ir * s,
+                               static_cast<F&&>(use));
+}
+
 __device__ __forceinline__ f2 f2_of(double v) { return f2_from_double(v, 0); }
 
 // Tables of irregular_group_w2 and of the apply that takes its pairs (read

@@ -147,11 +147,11 @@ __global__ void __launch_bounds__(MC_THREADS)
           const double qi = act ? v.w : 0.0;
           // column-scaled irregular set with the charge folded into its start
           // value (value (n, m) / P_n^m); P_n^m is applied once per chunk
-          irregular_group_w<double>(&tabs, s_iW, p, dx, dy, dz, qi,
-                                    [&](int t2, int n, int m, bool vld, double cr, double ci) {
-                                      ar[t2] += cr;
-                                      ai[t2] -= ci;
-                                    });
+          irregular_group_wu<double>(&tabs, s_iW, p, dx, dy, dz, qi,
+                                     [&](int t2, int n, int m, bool vld, double cr, double ci) {
+                                       ar[t2] += cr;
+                                       ai[t2] -= ci;
+                                     });
         }
       }
     }
