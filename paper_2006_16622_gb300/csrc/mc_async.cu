@@ -729,8 +729,8 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
             irregular_group_w<TE>(&tabs, s_iW, p, dx, dy, dz, f, [&](int t2, int n, int m, bool v, TE vr, TE vi) {
               if (se.valid && v) {
                 const int kk = rl_re(n, m);
-                atomicAdd(&Dt[kk], to_double(vr));
-                if (m) atomicAdd(&Dt[kk + 1], to_double(neg_bits(vi)));
+                red_add_f64(&Dt[kk], to_double(vr));
+                if (m) red_add_f64(&Dt[kk + 1], to_double(neg_bits(vi)));
               }
             });
           } else {

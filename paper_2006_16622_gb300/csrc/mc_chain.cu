@@ -954,8 +954,8 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
         irregular_group_s<TE>(&tabs, p, dx, dy, dz, f, [&](int t2, int n, int m, bool v, TE vr, TE vi) {
           if (se.valid && v) {
             const int kk = rl_re(n, m);
-            atomicAdd(&Lt[kk], to_double(vr));
-            if (m) atomicAdd(&Lt[kk + 1], to_double(neg_bits(vi)));
+            red_add_f64(&Lt[kk], to_double(vr));
+            if (m) red_add_f64(&Lt[kk + 1], to_double(neg_bits(vi)));
           }
         });
         if (prof_on && lane == 0) prof_item(rp.prof, 4, t_item);
