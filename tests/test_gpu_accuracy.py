@@ -6,7 +6,8 @@ local method at p = 25 (the paper's reference).  Checks: the GPU local
 method at p = 15 (the reference of bench.py --accuracy) is two orders below
 the p = 11 error; the error falls with p; at 12 expansion terms (p = 11) the
 mean error is below 1e-3 for both methods (the paper's operating point), with
-the local method the more accurate one at equal p.
+the local method the more accurate one at equal p.  The FP32-eval form of
+the local method meets the same bound at p = 11.
 """
 import numpy as np
 import pytest
@@ -36,8 +37,8 @@ def test_acceptance_probability_error_against_p25():
     ref.setup()
     p_ref = np.exp(-NACL_BETA * np.array([ref.propose(int(j), r) for j, r in zip(js, rn)]))
 
-    def mean_dp(p, mode):
-        ctx = mcfmm.Context(pos, q, a, L, p)
+    def mean_dp(p, mode, precision=mcfmm.FP64):
+        ctx = mcfmm.Context(pos, q, a, L, p, precision=precision)
         ctx.setup(mode)
         d = np.array([ctx.propose(int(j), r) for j, r in zip(js, rn)])
         ctx.close()
@@ -50,3 +51,7 @@ def test_acceptance_probability_error_against_p25():
     assert loc[15][0] < 0.2 * loc[11][0] and loc[15][1] < 5e-5
     assert loc[11][0] < 1e-3 and mm11[0] < 1e-3
     assert loc[11][0] < mm11[0]
+    # FP32 evaluation, FP64 accumulation: its rounding stays below the
+    # paper's acceptance-probability bound at its operating point
+    f32 = mean_dp(11, mcfmm.SETUP_P2L, mcfmm.FP32_EVAL)
+    assert f32[0] < 1e-3, f32

@@ -50,7 +50,11 @@ def dense():
 def _check_replay(rg, ro):
     assert ro["n_borderline"] == 0 and rg["borderline"] == 0
     assert np.array_equal(rg["j"], ro["j"])
-    err = np.abs(rg["dE"] - ro["dE"]) / np.maximum(1.0, np.abs(ro["dE"]))
+    # +inf (overlap, or a move out of a free-space box) on both sides alike
+    fin = np.isfinite(ro["dE"])
+    assert np.array_equal(np.isfinite(rg["dE"]), fin)
+    assert np.array_equal(rg["dE"][~fin], ro["dE"][~fin])
+    err = np.abs(rg["dE"][fin] - ro["dE"][fin]) / np.maximum(1.0, np.abs(ro["dE"][fin]))
     assert np.max(err) <= DE_TOL, np.max(err)
     assert np.array_equal(rg["acc"], ro["acc"])
 
@@ -175,3 +179,22 @@ def test_multipole_method_split_replays_oracle(dense):
         _check_replay(rg, ro)
         assert np.array_equal(g.positions(), o.positions())
         g.close()
+
+
+@pytest.mark.parametrize("schedule", [mcfmm.SCHEDULE_ASYNC, mcfmm.SCHEDULE_PHASED])
+def test_free_space_split_replays_oracle(schedule):
+    """Free space: near cells outside the box are skipped by every part; a
+    move leaving the box is rejected (+inf) on both sides."""
+    pos, q = uniform_system(N, A, seed=22)
+    o = O.System(pos, q, A, L, P_EXP, bc=mcfmm.BC_FREE)
+    o.setup()
+    steps = 800
+    ro = o.run(steps, seed=12, step0=0, beta=1.0, half_width=H)
+    g = mcfmm.Context(pos, q, A, L, P_EXP, bc=mcfmm.BC_FREE)
+    g.set_near_parts(3)
+    g.setup()
+    g.set_schedule(schedule)
+    rg = g.run(steps, seed=12, beta=1.0, half_width=H, log=True)
+    _check_replay(rg, ro)
+    assert np.array_equal(g.positions(), o.positions())
+    g.close()
