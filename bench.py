@@ -88,6 +88,8 @@ def parse():
     ap.add_argument("--accuracy", action="store_true",
                     help="run only the acceptance-probability study (relative error of P vs p)")
     ap.add_argument("--accuracy-configs", type=int, default=16)
+    ap.add_argument("--model-fit", action="store_true",
+                    help="run only the performance-model fit of Sec. 5.4 (propose and accept times vs N)")
     ap.add_argument("--accuracy-moves", type=int, default=1000)
     ap.add_argument("--huge-steps", type=int, default=1_000_000,
                     help="proposals timed per form on the N=1e6 workload")
@@ -995,10 +997,124 @@ def accuracy_study(args):
     print(json.dumps(out), flush=True)
 
 
+def model_fit_study():
+    """The performance model of Sec. 5.4, T(N) = tau + gamma L + kappa N/N_cell
+    + sigma N with N_cell = 8^(L-1), fitted by least squares to the time per
+    propose and per accept operation of both methods (FP64), measured in the
+    setting of Sec. 5.2: uniform random +-1 charges at the density of the
+    NaCl spacing (3.3 A), moves of +-0.25 A per axis, 12 expansion terms
+    (p = 11), N = 1e3..1e6, levels from L = floor(log8(alpha N)) with
+    alpha = 0.327 (local) and 0.138 (multipole), the optimal values of
+    Sec. 5.1.  The local method runs its plain schedule, whose accept phase
+    is Alg. L.2 after the decision (the speculative schedule moves that work
+    into the propose phase); the multipole method runs Alg. M.1 / M.2.
+    Times are the device timers of CTA 0 (propose: the proposal draw to the
+    decision; accept: the accept phase and its barrier, per accepted move).
+    Also the speed-up S(N) and its limit S_inf at nu = 0.438."""
+    import numpy as np
+    import torch
+
+    from paper_2006_16622_gb300 import mcfmm
+    from paper_2006_16622_gb300.workloads import uniform_system
+
+    mcfmm.load()
+    rho = 1.0 / 3.3 ** 3
+    p, h, beta, nu = 11, 0.25, 1.0, 0.438
+    sizes = [1000, 2000, 5000, 10_000, 20_000, 50_000, 100_000, 200_000, 500_000, 1_000_000]
+    # local method twice: its plain schedule (the paper's split: Alg. L.2 in
+    # the accept) and the speculative phased schedule of this implementation
+    # (the contributions computed during the propose phase, the accept adds)
+    methods = (("local", 0.327, mcfmm.SETUP_P2L, mcfmm.SCHEDULE_PLAIN),
+               ("local_spec", 0.327, mcfmm.SETUP_P2L, mcfmm.SCHEDULE_PHASED),
+               ("multipole", 0.138, mcfmm.SETUP_MULTIPOLE, None))
+    rows = []
+    t0 = time.perf_counter()
+    for n in sizes:
+        a = (n / rho) ** (1.0 / 3.0)
+        pos, q = uniform_system(n, a, seed=n)
+        for name, alpha, mode, sched in methods:
+            L = max(2, int(np.floor(np.log(alpha * n) / np.log(8.0))))
+            ctx = mcfmm.Context(pos, q, a, L, p, precision=mcfmm.FP64)
+            ctx.setup(mode)
+            if sched is not None:
+                ctx.set_schedule(sched)
+            ctx.run(2000, seed=1, beta=beta, half_width=h, stats=False)
+            ctx.profile(True)
+            ctx.profile_read()
+            ctx.run(5000, seed=2, beta=beta, half_width=h, stats=False)
+            pr = ctx.profile_read().astype(np.float64)
+            ctx.profile(False)
+            ctx.close()
+            steps, acc = max(pr[5], 1.0), max(pr[6], 1.0)
+            rows.append({"n": n, "method": name, "levels": L, "n_per_cell": n / 8.0 ** (L - 1),
+                         "propose_us": (pr[0] + pr[1] + pr[2]) / steps / 1e3,
+                         "accept_us": (pr[3] + pr[4]) / acc / 1e3, "acceptance": pr[6] / steps})
+    torch.cuda.synchronize()
+    # non-negative least squares (every term of the model is a cost); the
+    # columns are scaled to unit norm for the solve
+    try:
+        from scipy.optimize import nnls
+    except ImportError:  # pragma: no cover - scipy is part of the image
+        nnls = None
+    fits = {}
+    for name, _, _, _ in methods:
+        rs = [r for r in rows if r["method"] == name]
+        X = np.array([[1.0, r["levels"], r["n_per_cell"], r["n"]] for r in rs])
+        scale = np.linalg.norm(X, axis=0)
+        for stage in ("propose", "accept"):
+            y = np.array([r[f"{stage}_us"] for r in rs])
+            if nnls is not None:
+                cs, _ = nnls(X / scale, y)
+            else:
+                cs = np.clip(np.linalg.lstsq(X / scale, y, rcond=None)[0], 0.0, None)
+            coef = cs / scale
+            resid = y - X @ coef
+            fits[f"{name}_{stage}"] = {"tau": coef[0], "gamma": coef[1], "kappa": coef[2], "sigma": coef[3],
+                                       "rms_residual_us": float(np.sqrt(np.mean(resid ** 2)))}
+
+    def T(name, stage, n, alpha):
+        L = max(2, int(np.floor(np.log(alpha * n) / np.log(8.0))))
+        f = fits[f"{name}_{stage}"]
+        return f["tau"] + f["gamma"] * L + f["kappa"] * n / 8.0 ** (L - 1) + f["sigma"] * n
+
+    f = fits
+    speedup, s_inf = {}, {}
+    for loc in ("local", "local_spec"):
+        sp = {}
+        for n in sizes:
+            mp = T("multipole", "propose", n, 0.138) + nu * T("multipole", "accept", n, 0.138)
+            lo = T(loc, "propose", n, 0.327) + nu * T(loc, "accept", n, 0.327)
+            sp[str(n)] = mp / lo
+        speedup[loc] = sp
+        den = f[f"{loc}_propose"]["gamma"] + nu * f[f"{loc}_accept"]["gamma"]
+        num = f["multipole_propose"]["gamma"] + nu * f["multipole_accept"]["gamma"]
+        s_inf[loc] = num / den if den > 0 else None
+    # the measured ratio of the step times (propose + nu accept) per size
+    measured = {}
+    for loc in ("local", "local_spec"):
+        m = {}
+        for n in sizes:
+            r_l = next(r for r in rows if r["n"] == n and r["method"] == loc)
+            r_m = next(r for r in rows if r["n"] == n and r["method"] == "multipole")
+            m[str(n)] = ((r_m["propose_us"] + nu * r_m["accept_us"])
+                         / (r_l["propose_us"] + nu * r_l["accept_us"]))
+        measured[loc] = m
+    out = {"metric": "performance model of Sec. 5.4 fitted to GPU propose/accept times",
+           "workload": "uniform +-1 charges, NaCl density (spacing 3.3 A), p = 11, h = 0.25 A, FP64",
+           "rows": rows, "fits": fits, "speedup_nu_0.438": speedup, "s_inf": s_inf,
+           "measured_speedup_nu_0.438": measured,
+           "paper": {"s_inf": 2.02, "measured_speedup_range": [1.18, 1.34]},
+           "seconds": time.perf_counter() - t0}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.accuracy:
         accuracy_study(args)
+        return
+    if args.model_fit:
+        model_fit_study()
         return
     if args.profile:
         profile_launch(args)
