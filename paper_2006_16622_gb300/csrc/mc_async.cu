@@ -130,7 +130,10 @@ __device__ __forceinline__ bool counter_wait(unsigned long long* ctr, unsigned l
       const unsigned long long t0 = mc_globaltimer();
       unsigned spins = 0;
       while (true) {
-        if (spins >= 2u) __nanosleep(100);
+        // a few polls back to back, then a short back-off (measured on
+        // GB300: +0.4 % over backing off from the third poll; longer
+        // back-offs delay these waits, which are on the step's critical path)
+        if (spins >= 8u) __nanosleep(100);
         v = ld_relaxed_b64(ctr);
         if (v >= target) break;
         if ((++spins & 31u) == 0u) {
