@@ -997,6 +997,37 @@ def accuracy_study(args):
     print(json.dumps(out), flush=True)
 
 
+def model_levels(n, alpha):
+    """L = floor(log8(alpha N)), at least 2 (Sec. 5.1's rule for the levels)."""
+    import math
+    return max(2, int(math.floor(math.log(alpha * n) / math.log(8.0) + 1e-12)))
+
+
+def performance_model(f, n, L):
+    """T = tau + gamma L + kappa N / N_cell + sigma N, N_cell = 8^(L-1) (Sec. 5.4)."""
+    return f["tau"] + f["gamma"] * L + f["kappa"] * n / 8.0 ** (L - 1) + f["sigma"] * n
+
+
+def fit_performance_model(rows, key):
+    """Non-negative least-squares fit of the Sec. 5.4 model to rows of
+    {"n", "levels", key} (every term of the model is a cost; the columns are
+    scaled to unit norm for the solve).  Returns tau, gamma, kappa, sigma and
+    the rms residual."""
+    import numpy as np
+    X = np.array([[1.0, r["levels"], r["n"] / 8.0 ** (r["levels"] - 1), r["n"]] for r in rows])
+    y = np.array([r[key] for r in rows], dtype=np.float64)
+    scale = np.linalg.norm(X, axis=0)
+    try:
+        from scipy.optimize import nnls
+        cs, _ = nnls(X / scale, y)
+    except ImportError:  # pragma: no cover - scipy is part of the image
+        cs = np.clip(np.linalg.lstsq(X / scale, y, rcond=None)[0], 0.0, None)
+    coef = cs / scale
+    resid = y - X @ coef
+    return {"tau": float(coef[0]), "gamma": float(coef[1]), "kappa": float(coef[2]), "sigma": float(coef[3]),
+            "rms_residual_us": float(np.sqrt(np.mean(resid ** 2)))}
+
+
 def model_fit_study():
     """The performance model of Sec. 5.4, T(N) = tau + gamma L + kappa N/N_cell
     + sigma N with N_cell = 8^(L-1), fitted by least squares to the time per
@@ -1033,7 +1064,7 @@ def model_fit_study():
         a = (n / rho) ** (1.0 / 3.0)
         pos, q = uniform_system(n, a, seed=n)
         for name, alpha, mode, sched in methods:
-            L = max(2, int(np.floor(np.log(alpha * n) / np.log(8.0))))
+            L = model_levels(n, alpha)
             ctx = mcfmm.Context(pos, q, a, L, p, precision=mcfmm.FP64)
             ctx.setup(mode)
             if sched is not None:
@@ -1050,32 +1081,14 @@ def model_fit_study():
                          "propose_us": (pr[0] + pr[1] + pr[2]) / steps / 1e3,
                          "accept_us": (pr[3] + pr[4]) / acc / 1e3, "acceptance": pr[6] / steps})
     torch.cuda.synchronize()
-    # non-negative least squares (every term of the model is a cost); the
-    # columns are scaled to unit norm for the solve
-    try:
-        from scipy.optimize import nnls
-    except ImportError:  # pragma: no cover - scipy is part of the image
-        nnls = None
     fits = {}
     for name, _, _, _ in methods:
         rs = [r for r in rows if r["method"] == name]
-        X = np.array([[1.0, r["levels"], r["n_per_cell"], r["n"]] for r in rs])
-        scale = np.linalg.norm(X, axis=0)
         for stage in ("propose", "accept"):
-            y = np.array([r[f"{stage}_us"] for r in rs])
-            if nnls is not None:
-                cs, _ = nnls(X / scale, y)
-            else:
-                cs = np.clip(np.linalg.lstsq(X / scale, y, rcond=None)[0], 0.0, None)
-            coef = cs / scale
-            resid = y - X @ coef
-            fits[f"{name}_{stage}"] = {"tau": coef[0], "gamma": coef[1], "kappa": coef[2], "sigma": coef[3],
-                                       "rms_residual_us": float(np.sqrt(np.mean(resid ** 2)))}
+            fits[f"{name}_{stage}"] = fit_performance_model(rs, f"{stage}_us")
 
     def T(name, stage, n, alpha):
-        L = max(2, int(np.floor(np.log(alpha * n) / np.log(8.0))))
-        f = fits[f"{name}_{stage}"]
-        return f["tau"] + f["gamma"] * L + f["kappa"] * n / 8.0 ** (L - 1) + f["sigma"] * n
+        return performance_model(fits[f"{name}_{stage}"], n, model_levels(n, alpha))
 
     f = fits
     speedup, s_inf = {}, {}

@@ -93,3 +93,35 @@ def test_result_line_fits_the_stored_tail(bench):
         assert k in back["forms"] and k in back["roofline_frac"]
     for k in ("metric", "value", "unit", "roofline", "cpu_baseline", "e2e", "clocks", "gpu_launches"):
         assert k in back
+
+
+def test_performance_model_fit_recovers_table_1():
+    """The Sec. 5.4 fit, fed times generated from the paper's Table 1
+    coefficients (local propose and multipole propose) over the paper's
+    N = 1e3..1e6 with its level rule, returns those coefficients, and the
+    asymptotic speed-up of Table 1's gammas at nu = 0.438 is the paper's
+    S_inf = 2.02."""
+    import bench
+    table = {"loc_prop": (304.01, 9.92, 0.61, 4.12e-5), "loc_acc": (225.80, 239.99, 0.19, 4.37e-5),
+             "mp_prop": (89.15, 228.40, 0.50, 1.49e-4), "mp_acc": (436.71, 8.12, 0.27, 7.11e-6)}
+    sizes = [int(round(10 ** (3 + 0.25 * k))) for k in range(13)]
+    for key, (tau, gamma, kappa, sigma) in table.items():
+        alpha = 0.327 if key.startswith("loc") else 0.138
+        f = {"tau": tau, "gamma": gamma, "kappa": kappa, "sigma": sigma}
+        rows = [{"n": n, "levels": bench.model_levels(n, alpha),
+                 "t": bench.performance_model(f, n, bench.model_levels(n, alpha))} for n in sizes]
+        got = bench.fit_performance_model(rows, "t")
+        for name in ("tau", "gamma", "kappa", "sigma"):
+            assert abs(got[name] - f[name]) <= 1e-6 * max(1.0, abs(f[name])), (key, name, got[name])
+        assert got["rms_residual_us"] < 1e-6
+    nu = 0.438
+    s_inf = (table["mp_prop"][1] + nu * table["mp_acc"][1]) / (table["loc_prop"][1] + nu * table["loc_acc"][1])
+    assert abs(s_inf - 2.02) < 0.005
+
+
+def test_model_levels_follow_the_paper_rule():
+    import bench
+    # Sec. 5.1: L = floor(log8(alpha N)); the NaCl 46^3 system with the local
+    # alpha gives the paper's L = 4
+    assert bench.model_levels(97_336, 0.327) == 4
+    assert bench.model_levels(1000, 0.327) == 2 and bench.model_levels(10 ** 6, 0.327) == 6
