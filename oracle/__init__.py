@@ -63,6 +63,7 @@ def lib():
             L.orc_setup.argtypes = [_P]
             L.orc_setup_fmm.argtypes = [_P]
             L.orc_fmm_local_cell.argtypes = [_P, ctypes.c_int, _P, _P]
+            L.orc_local_cell_direct.argtypes = [_P, ctypes.c_int, _P, _P]
             L.orc_setup_multipole.argtypes = [_P]
             L.orc_set_lj.argtypes = [_P, _D, _D, _D]
             L.orc_get_multipole.argtypes = [_P, ctypes.c_int, _P]
@@ -242,6 +243,15 @@ class System:
         out = np.zeros(self.C)
         if lib().orc_fmm_local_cell(self._h, level, _ptr(cc), _ptr(out)) != 0:
             raise ValueError("bad level")
+        return out
+
+    def local_cell_direct(self, level, c):
+        """Alg. L.3 expansion of one cell by its definition (no setup
+        needed), real layout, paper normalisation."""
+        cc = np.ascontiguousarray(np.asarray(c, dtype=np.int32))
+        out = np.zeros(self.C)
+        if lib().orc_local_cell_direct(self._h, level, _ptr(cc), _ptr(out)) != 0:
+            raise ValueError("bad level or cell")
         return out
 
     def propose(self, j, rnew):

@@ -751,6 +751,56 @@ int orc_get_multipole(const orc_sys *s, int level, double *out) {
 
 /* one cell's FMM-variant expansion (real layout), all from the particles:
  * for sampled checks at sizes where the whole pass is too slow */
+/* Psi^Delta of one target cell c of level l by its definition (Alg. L.3,
+ * Eq. 1): the sum over the entries f of IL(c) -- each the image of a
+ * canonical cell shifted by sh boxes -- of the charges i of that cell,
+ * q_i conj It(r_i + sh a - R_c).  By the symmetry of the interaction list
+ * this is the value setup_local scatters into cell c; here it is gathered
+ * for one cell (O(N) to find the charges), for sampled cells of systems too
+ * large for the full setup. */
+int orc_local_cell_direct(orc_sys *s, int l, const int c[3], double *out) {
+  if (l < 2 || l > s->L) return -1;
+  const int nl = ncell_axis(l), C = s->C;
+  for (int d = 0; d < 3; d++)
+    if (c[d] < 0 || c[d] >= nl) return -1;
+  int off[189][3], src[189], shf[189][3];
+  const int nIL = il_offsets(c, off);
+  /* entries by canonical source cell: first[cell] -> entry, nxt[entry] */
+  int *first = (int *)malloc(sizeof(int) * (size_t)nl * nl * nl);
+  int nxt[189];
+  for (int64_t k = 0; k < (int64_t)nl * nl * nl; k++) first[k] = -1;
+  for (int k = 0; k < nIL; k++) {
+    const int e[3] = {c[0] + off[k][0], c[1] + off[k][1], c[2] + off[k][2]};
+    int cc[3];
+    src[k] = -1;
+    if (!wrap_cell(s, nl, e, cc, shf[k])) continue;
+    src[k] = lin(nl, cc);
+    nxt[k] = first[src[k]];
+    first[src[k]] = k;
+  }
+  double Rc[3];
+  cell_centre(s, l, c, Rc);
+  cplx *Lb = (cplx *)calloc((size_t)C, sizeof(cplx));
+  cplx *irr = (cplx *)malloc(sizeof(cplx) * C);
+  for (int64_t i = 0; i < s->n; i++) {
+    int cf[3], ci[3];
+    finest_cell(s, &s->pos[3 * i], cf);
+    for (int d = 0; d < 3; d++) ci[d] = cf[d] >> (s->L - l);
+    for (int k = first[lin(nl, ci)]; k >= 0; k = nxt[k]) {
+      double d3[3];
+      for (int t = 0; t < 3; t++) d3[t] = s->pos[3 * i + t] + shf[k][t] * s->a - Rc[t];
+      irregular_table(s->p, d3, irr);
+      for (int nn = 0; nn <= s->p; nn++)
+        for (int m = -nn; m <= nn; m++) Lb[IDX(nn, m)] += s->q[i] * irr[IDX(nn, -m)];
+    }
+  }
+  to_real_layout(s->p, Lb, out);
+  free(irr);
+  free(Lb);
+  free(first);
+  return 0;
+}
+
 int orc_fmm_local_cell(orc_sys *s, int l, const int c[3], double *out) {
   if (l < 2 || l > s->L) return -1;
   cplx *Lb = (cplx *)malloc(sizeof(cplx) * s->C);

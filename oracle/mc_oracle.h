@@ -58,6 +58,10 @@ void orc_setup_fmm(orc_sys *s);
 /* one cell's FMM-variant expansion (real layout), source multipoles taken
  * directly from the charges; -1 for a bad level */
 int orc_fmm_local_cell(orc_sys *s, int level, const int c[3], double *out);
+/* one cell's Alg. L.3 expansion (real layout) by its definition, gathered
+ * from the charges of its interaction list; needs no setup; -1 for a bad
+ * level or cell */
+int orc_local_cell_direct(orc_sys *s, int level, const int c[3], double *out);
 /* the multipole method (Sec. 3.3, alternative algorithm): Alg. M.3 + K/E +
  * U0; afterwards propose/accept/run/energy follow Alg. M.1/M.2.  orc_setup
  * or orc_setup_fmm switch back to the local method. */

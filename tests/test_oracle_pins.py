@@ -573,3 +573,31 @@ def test_lennard_jones_energy_and_moves_match_pair_sums():
         assert abs((s.propose(j, rn) - base.propose(j, rn)) - dlj) < 1e-10
     with pytest.raises(ValueError):
         s.set_lj(eps, sig, 12.5)  # beyond the finest cell width
+
+
+@pytest.mark.parametrize("bc", [O.BC_PBC, O.BC_FREE])
+def test_local_cell_direct_equals_the_setup(bc):
+    """Alg. L.3 for one cell by its definition (gathered from the charges of
+    its interaction list, no setup) equals the cell of the full setup
+    (scattered particle by particle), on every level: the two are the same
+    sum in another order, through the symmetry of the interaction list."""
+    n, a, L, p = 700, 9.0, 4, 7
+    pos, q = uniform_system(n, a, seed=31)
+    o = O.System(pos, q, a, L, p, bc=bc)
+    d = O.System(pos, q, a, L, p, bc=bc)  # never set up
+    o.setup()
+    rng = np.random.default_rng(5)
+    for lev in range(2, L + 1):
+        nl = 1 << (lev - 1)
+        full = o.local(lev)
+        scale = np.max(np.abs(full))
+        cells = [np.array(c) for c in np.ndindex(nl, nl, nl)] if nl <= 4 else \
+            [rng.integers(0, nl, size=3) for _ in range(12)]
+        for c in cells:
+            got = d.local_cell_direct(lev, c)
+            ref = full[(c[0] * nl + c[1]) * nl + c[2]]
+            assert np.max(np.abs(got - ref)) <= 1e-13 * scale, (lev, c)
+    with pytest.raises(ValueError):
+        d.local_cell_direct(1, [0, 0, 0])
+    with pytest.raises(ValueError):
+        d.local_cell_direct(L, [1 << (L - 1), 0, 0])
