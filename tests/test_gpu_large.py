@@ -9,7 +9,9 @@ same system up (about a minute of one host core), then
     1e-10 max(1, |dE|) and every decision identical,
   - properties that hold at any size: the running energy stays within
     truncation of a fresh evaluation, and a fresh GPU setup on the final
-    positions equals the incrementally updated expansions.
+    positions equals the incrementally updated expansions,
+  - the FP32-eval form from the oracle's state after the replay: the oracle
+    follows its decisions and every dE is within the form's tolerance.
 """
 import numpy as np
 import pytest
@@ -86,3 +88,31 @@ def test_large_properties_after_a_long_chain(large_pair):
         A, B = g.local(lev), f.local(lev)
         assert np.max(np.abs(A - B)) <= 1e-11 * np.max(np.abs(B)), lev
     f.close()
+
+
+def test_large_fp32_eval_follows_oracle(large_pair):
+    """The FP32-eval form at the full size (its default phased schedule on
+    the bench's grid), from the oracle's current state: the oracle follows
+    the GPU's decisions for 300 proposals; beta |dE_gpu - dE_oracle| has
+    p95 <= 1e-4 and max <= 1e-3, the form's stated tolerance, and a decision
+    may differ from the oracle's only within that error of the threshold."""
+    W, g, o, pos, q = large_pair
+    start = o.positions()
+    f = mcfmm.Context(start, q, W.a, W.levels, W.p, precision=mcfmm.FP32_EVAL)
+    f.setup()
+    steps, seed = 300, W.seed + 5
+    rg = f.run(steps, seed=seed, beta=W.beta, half_width=W.half_width, log=True)
+    fin = f.positions()
+    f.close()
+    r = o.run_follow(rg["acc"], seed=seed, step0=0, chain=0, beta=W.beta, half_width=W.half_width)
+    assert np.array_equal(rg["j"], r["j"])
+    both = np.isfinite(rg["dE"]) & np.isfinite(r["dE"])
+    assert np.array_equal(np.isfinite(rg["dE"]), np.isfinite(r["dE"]))
+    e = W.beta * np.abs(rg["dE"][both] - r["dE"][both])
+    assert np.percentile(e, 95) <= 1e-4, np.percentile(e, 95)
+    assert e.max() <= 1e-3, e.max()
+    for t in np.nonzero(rg["acc"].astype(bool) != (r["acc"].astype(bool)))[0]:
+        _, _, u = O.proposal(len(q), W.half_width, seed, int(t), 0)
+        gap = abs(np.log(u) + W.beta * r["dE"][t])
+        assert gap <= W.beta * abs(rg["dE"][t] - r["dE"][t]) + 1e-12, (t, gap)
+    assert np.array_equal(fin, o.positions())
