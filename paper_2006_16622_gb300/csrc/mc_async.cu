@@ -898,10 +898,8 @@ __device__ __forceinline__ void async_body(const McSys* __restrict__ sysp, RunPa
             ptype = 1;
             const int k0 = it - iN;
             if (!idle) {
-              const int kb = same ? k0 : (k0 % 54);
-              const int k = kb % 27;
-              const int side = same ? 2 : (kb / 27);  // 0 old, 1 new, 2 both
-              const int part = same ? k0 / 27 : k0 / 54, nparts = same ? 2 * nNP : nNP;
+              const NearPart np = near_part(k0, same, nNP, 2 * nNP);
+              const int k = np.k, side = np.side, part = np.part, nparts = np.nparts;
               if (!item_near<TE>(S, g, off, k, side, part, nparts, pbc, lane,
                                  [&](int, int, int) {
                                    const bool okw = need_state();

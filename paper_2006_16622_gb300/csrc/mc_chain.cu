@@ -652,10 +652,8 @@ __device__ __forceinline__ void chain_body(const McSys* __restrict__ sysp, RunPa
         // ---- N: Alg. 1 over one near cell (27 cells of the extended domain)
         ptype = 1;
         const int k0 = it - iN;
-        const int kb = same ? k0 : (k0 % 54);
-        const int k = kb % 27;
-        const int side = same ? 2 : (kb / 27);  // 0 old, 1 new, 2 both
-        const int part = same ? k0 / 27 : k0 / 54, nparts = same ? nNsame : nNP;
+        const NearPart np = near_part(k0, same, nNP, nNsame);
+        const int k = np.k, side = np.side, part = np.part, nparts = np.nparts;
         item_near<TE>(S, g, s_off, k, side, part, nparts, pbc, lane,
                       [&](int, int, int) {
                         need_state();

@@ -119,3 +119,31 @@ __device__ __forceinline__ SmallEntry small_entry(const unsigned short (*il)[189
   for (int d = 0; d < 3; d++) se.t3[d] = mc_wrap_coord(e[d], nl);
   return se;
 }
+
+// Near-field items of a step (Alg. 1 split over several items per near
+// cell): item k0 takes near cell k (0..26) of the side `side` (0: r, 1: r',
+// 2: both, when r and r' share their finest cell) and the slot blocks part,
+// part + nparts, ... (32 slots each) of that cell.  With different cells the
+// 54 nparts items are (cell, side) x nparts; with a shared cell the first
+// 27 nsame items are cell x nsame (items beyond get k = -1, no work).
+struct NearPart {
+  int k, side, part, nparts;
+};
+
+__device__ __forceinline__ NearPart near_part(int k0, bool same, int nparts, int nsame) {
+  NearPart r;
+  if (same) {
+    r.k = k0 % 27;
+    r.side = 2;
+    r.part = k0 / 27;
+    r.nparts = nsame;
+    if (r.part >= nsame) r.k = -1;
+  } else {
+    const int kb = k0 % 54;
+    r.k = kb % 27;
+    r.side = kb / 27;
+    r.part = k0 / 54;
+    r.nparts = nparts;
+  }
+  return r;
+}
